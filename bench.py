@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 pattern-defeating sort (Peters, arXiv 2106.05123) on synthetic keys.
+
+One step = one full sort (probe, distribution levels, base sorts) of one array resident in HBM.
+Default workload: n = 2^28 int32 keys drawn i.i.d. uniform over the int32 range (SplitMix64,
+fixed seed).  Other workloads (--workload): the 2^20 case, the 2^24 pattern sweep, the 2^27
+key/value pairs.
+
+Prints ONE JSON line (rank 0).  `value` is keys sorted per second over all ranks (Gkeys/s);
+each rank sorts its own array (independent problems, weak scaling).  Timing: W warm-up steps,
+then K steps, each bracketed by CUDA events on the sorting stream; the input is restored from
+a pristine device copy and L2 is flushed (a 512 MiB write) between steps, outside the events.
+
+Extra keys: `roofline` (dominant kernel: algorithmic bytes / its event-timed duration vs the
+measured HBM copy bandwidth), `cpu_baseline` (the CPU oracle on one host core, on a bounded
+sample), `e2e` (same metric through the host-buffer C-ABI call pdq_sort_host, copies included),
+`clocks` (nvidia-smi sampled during the timed region), `gpu_launches` (library kernels launched
+in the timed region).
+
+--impl reference times the CPU oracle itself on the host (rank 0 only), one bounded sample per
+step, with the same metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOADS = {
+    # name: (description, n, key dtype, value dtype or None)
+    "uniform_i32_2p28": ("uniform int32 keys, n=2^28", 1 << 28, np.int32, None),
+    "uniform_i32_2p20": ("uniform int32 keys, n=2^20", 1 << 20, np.int32, None),
+    "sweep_i32_2p24": ("pattern sweep, 8 int32 patterns of n=2^24 each per step", 1 << 24, np.int32, None),
+    "pairs_u64_zipf_2p27": ("uint64 Zipf(1.1) keys over 256 values + uint32 index, n=2^27", 1 << 27,
+                            np.uint64, np.uint32),
+    "pairs_f32_normal_2p27": ("float32 N(0,1) keys with NaN/-0/inf + uint32 index, n=2^27", 1 << 27,
+                              np.float32, np.uint32),
+}
+
+
+def make_inputs(name: str, rank: int):
+    _, n, kdt, vdt = WORKLOADS[name]
+    seed = workloads.config_seed(0) ^ rank
+    if name.startswith("uniform"):
+        return [(workloads.uniform_bits(n, kdt, seed), None)]
+    if name == "sweep_i32_2p24":
+        return [(workloads.pattern(p, n, workloads.config_seed(1) ^ rank, dtype=np.int32), None)
+                for p in workloads.SWEEP_PATTERNS]
+    if name == "pairs_u64_zipf_2p27":
+        return [workloads.zipf_u64_pairs(n, workloads.config_seed(2) ^ rank)]
+    if name == "pairs_f32_normal_2p27":
+        return [workloads.normal_f32_specials(n, workloads.config_seed(2) ^ rank)]
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------- helpers
+def measured_peak_gbs() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_05123_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str) -> float | None:
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was captured on
+    the current kernel sources (profiles/traffic.txt lines: kernel workload bytes src_hash)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = kernel_source_hash()
+    for line in open(p):
+        m = re.match(r"\s*kernel=(\S+)\s+workload=(\S+)\s+bytes_per_launch=(\S+)\s+src=(\S+)", line)
+        if m and m.group(1) == kernel and m.group(2) == workload and m.group(4) == cur:
+            return float(m.group(3))
+    return None
+
+
+def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
+    """The CPU oracle (single-threaded, as it stands) on a bounded sample of the workload."""
+    import oracle
+    inputs = make_inputs_small(name)
+    total_keys, t_total, reps = 0, 0.0, 0
+    while t_total < budget_s or reps < 1:
+        for k, v in inputs:
+            kk = k.copy()
+            vv = v.copy() if v is not None else None
+            t0 = time.perf_counter()
+            if vv is None:
+                oracle.pdqsort(kk)
+            else:
+                oracle.pdqsort_pairs(kk, vv)
+            t_total += time.perf_counter() - t0
+            total_keys += k.size
+        reps += 1
+    n_sample = inputs[0][0].size
+    return {"value": total_keys / t_total / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(inputs)} array(s) of {n_sample} keys from the same generator, "
+                      f"{reps} repetition(s), {t_total:.1f} s of single-core CPU time"}
+
+
+def make_inputs_small(name: str):
+    """Bounded samples of each workload for the CPU oracle (2^24 keys, or 2^22 for pairs)."""
+    _, n, kdt, vdt = WORKLOADS[name]
+    m = min(n, 1 << 24) if vdt is None else min(n, 1 << 22)
+    if name.startswith("uniform"):
+        return [(workloads.uniform_bits(m, kdt, workloads.config_seed(0)), None)]
+    if name == "sweep_i32_2p24":
+        m = 1 << 22
+        return [(workloads.pattern(p, m, workloads.config_seed(1), dtype=np.int32), None)
+                for p in workloads.SWEEP_PATTERNS]
+    if name == "pairs_u64_zipf_2p27":
+        return [workloads.zipf_u64_pairs(m, workloads.config_seed(2))]
+    return [workloads.normal_f32_specials(m, workloads.config_seed(2))]
+
+
+# ----------------------------------------------------------------------------------- reference arm
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    inputs = make_inputs_small(args.workload)
+    import oracle
+    times, keys = [], 0
+    for step in range(args.warmup + args.steps):
+        t = 0.0
+        nk = 0
+        for k, v in inputs:
+            kk = k.copy()
+            vv = v.copy() if v is not None else None
+            t0 = time.perf_counter()
+            if vv is None:
+                oracle.pdqsort(kk)
+            else:
+                oracle.pdqsort_pairs(kk, vv)
+            t += time.perf_counter() - t0
+            nk += k.size
+        if step >= args.warmup:
+            times.append(t)
+            keys += nk
+    tot = sum(times)
+    value = keys / tot / 1e9
+    desc = WORKLOADS[args.workload][0]
+    sample = (f"each step: {len(inputs)} array(s) of {inputs[0][0].size} keys drawn like the "
+              f"workload ({desc}), single-threaded oracle")
+    line = {"metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args.workload),
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "description": desc, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def dtype_name(name: str) -> str:
+    _, _, kdt, vdt = WORKLOADS[name]
+    s = {np.int32: "int32", np.uint64: "uint64", np.float32: "f32"}[kdt]
+    return s + ("+u32" if vdt is not None else "")
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uniform_i32_2p28", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    bench_gpu(args, rank, world)
+
+
+def bench_gpu(args, rank: int, world: int) -> None:
+    import torch
+    import paper_2106_05123_gb300 as pdq
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    desc, n, kdt, vdt = WORKLOADS[args.workload]
+    host_inputs = make_inputs(args.workload, rank)
+    code = {np.int32: pdq.PDQ_I32, np.uint64: pdq.PDQ_U64, np.float32: pdq.PDQ_F32}[kdt]
+    kb = np.dtype(kdt).itemsize
+    vb = np.dtype(vdt).itemsize if vdt is not None else 0
+    carrier = {4: np.int32, 8: np.int64}
+
+    def dev(a):
+        return torch.from_numpy(a.view(carrier[a.dtype.itemsize]) if a.dtype != np.float32 else a).cuda()
+
+    pristine = [(dev(k), dev(v) if v is not None else None) for k, v in host_inputs]
+    work_k = torch.empty_like(pristine[0][0])
+    work_v = torch.empty_like(pristine[0][1]) if vb else None
+    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb)), dtype=torch.uint8, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_sort(i):
+        if vb:
+            return pdq.pdq_sort_pairs(work_k, work_v, ws, key_dtype=code)
+        return pdq.pdq_sort_keys(work_k, ws, key_dtype=code)
+
+    def step(timed_events=None):
+        st = None
+        for i, (pk, pv) in enumerate(pristine):
+            work_k.copy_(pk)
+            if vb:
+                work_v.copy_(pv)
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = one_sort(i)
+            e1.record(stream)
+            if timed_events is not None:
+                timed_events.append((e0, e1))
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # correctness guard on the last warm-up result (properties that hold at any size)
+    if not vb and kdt == np.int32:
+        assert bool((work_k[1:] >= work_k[:-1]).all().item()), "output not sorted"
+
+    sampler = ClockSampler(local)
+    events = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = pdq.launch_count()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(events)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    launches = pdq.launch_count() - l0
+    if dist is not None:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in events)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    keys_per_rank = n * len(pristine) * args.steps
+    value = keys_per_rank * world / (total_ms * 1e-3) / 1e9
+
+    # dominant kernel: one more (untimed) step with the library's per-kernel event timing
+    pdq.profile_reset()
+    pdq.profile_enable(True)
+    step()
+    torch.cuda.synchronize()
+    prof = pdq.profile_read()
+    pdq.profile_enable(False)
+    roofline = None
+    if prof:
+        dom, (dms, dcnt, dbytes) = max(prof.items(), key=lambda kv: kv[1][0])
+        peak, peak_src = measured_peak_gbs()
+        achieved = dbytes / (dms * 1e-3) / 1e9 if dms > 0 else 0.0
+        traffic = ncu_traffic(dom, args.workload)
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "algorithmic_bytes_per_launch": dbytes / max(1, dcnt),
+                    "ms_per_launch": dms / max(1, dcnt), "launches_per_step": dcnt,
+                    "share_of_step": dms / max(1e-9, sum(v[0] for v in prof.values())),
+                    "kernels": {k: {"ms": v[0], "launches": v[1], "alg_bytes": v[2]}
+                                for k, v in prof.items()}}
+
+    # end to end through the host-buffer call (pinned host memory, copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.empty(pristine[0][0].shape, dtype=pristine[0][0].dtype, pin_memory=True)
+        hv = torch.empty(pristine[0][1].shape, dtype=pristine[0][1].dtype, pin_memory=True) if vb else None
+        src_k = [torch.from_numpy(k.view(carrier[k.dtype.itemsize]) if k.dtype != np.float32 else k)
+                 for k, _ in host_inputs]
+        src_v = [torch.from_numpy(v.view(carrier[v.dtype.itemsize])) if v is not None else None
+                 for _, v in host_inputs]
+        e2e_steps = max(1, min(args.steps, 3))
+        t_e2e = 0.0
+        for s in range(e2e_steps + 1):
+            for i in range(len(src_k)):
+                hk.copy_(src_k[i])
+                if vb:
+                    hv.copy_(src_v[i])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                pdq.pdq_sort_host(hk, work_k, ws, h_vals=hv, d_vals=work_v)  # returns after D2H
+                t1 = time.perf_counter()
+                if s > 0:
+                    t_e2e += t1 - t0
+        e2e = {"value": n * len(src_k) * e2e_steps * world / t_e2e / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": n * (kb + vb) * len(src_k),
+               "d2h_bytes_per_step": n * (kb + vb) * len(src_k),
+               "api": "pdq_sort_host", "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {"metric": "Gkeys/s", "value": value, "unit": "Gkeys/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype_name(args.workload),
+                "data": "synthetic",
+                "config": {"workload": args.workload, "description": desc, "n": n,
+                           "arrays_per_step": len(pristine), "key_bytes": kb, "value_bytes": vb,
+                           "l2": "flushed (512 MiB write) and input restored between steps; "
+                                 "inputs larger than L2",
+                           "parallelism": f"{world} independent sorts (one per GPU)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches, "wall_s_timed_region": t_wall}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

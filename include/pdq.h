@@ -1,0 +1,132 @@
+/*
+ * pdq.h -- C ABI of the GB300 (sm_103a) pattern-defeating sort library.
+ *
+ * Operation (Peters, "Pattern-defeating Quicksort", arXiv 2106.05123, Sec. 1 and Sec. 3):
+ * sort a contiguous array in place, ascending, unstable, under a strict weak order.  Here the
+ * order is numeric for int32/uint32/int64/uint64 keys and IEEE 754-2008 totalOrder for float32
+ * keys (a total order on bit patterns: -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  The
+ * sorted key array is therefore unique and every call produces it bit for bit.  With a value
+ * payload, each value stays with its key; the order of values inside a run of equal keys is
+ * unspecified (the sort is unstable, Sec. 1).
+ *
+ * The GPU method keeps the paper's heuristics in data-parallel form:
+ *   - equal keys: a splitter that repeats, or any key equal to a splitter, lands in an equality
+ *     bucket that is final at once (Sec. 3, Lemma 4 / Theorem 1: O(nk) for k distinct keys);
+ *   - sorted / reverse-sorted input exits after a probe, reversing in place when descending
+ *     (Sec. 5.2);
+ *   - a bucket that keeps more than 7/8 of its parent is a bad split; each subtree has a
+ *     counter starting at floor(log2 n), and a bucket whose counter reaches 0 is sorted by a
+ *     merge-path merge sort, the O(n log n) fallback (Sec. 4.1, Theorem 2);
+ *   - fresh splitter samples after a bad split (Sec. 4.2);
+ *   - small buckets are sorted in shared memory (Sec. 5.1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are HOST pointers.
+ *   - Calls are asynchronous on `cuda_stream` (a cudaStream_t; NULL = legacy default stream)
+ *     except that the plain paths read a few small counters back from the device between
+ *     distribution levels, which synchronises the stream.  Host-side argument errors return at
+ *     once without touching the device.
+ *   - Workspace: caller-provided device memory of at least pdq_workspace_bytes(...) bytes,
+ *     256-byte aligned.  The library allocates no device memory of its own, except the
+ *     segmented path's CUDA-graph cache (see pdq_sort_segmented).
+ *   - n must be < 2^32.  n = 0 and n = 1 are no-ops.  value_bytes is 4 or 8.
+ *   - Return value: PDQ_OK or a negative pdq_status; pdq_last_error() gives a message (per
+ *     host thread).  After PDQ_ERR_CUDA / PDQ_ERR_TIMEOUT / PDQ_ERR_INTERNAL the arrays hold
+ *     an unspecified permutation of their input pairs.
+ *   - stats (nullable): filled on return with counters of the work done.
+ */
+#ifndef PDQ_H_
+#define PDQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PDQ_I32 = 0, PDQ_U32 = 1, PDQ_I64 = 2, PDQ_U64 = 3, PDQ_F32 = 4 } pdq_dtype;
+
+typedef enum {
+  PDQ_OK = 0,
+  PDQ_ERR_ARG = -1,        /* bad pointer, size, alignment or value_bytes */
+  PDQ_ERR_DTYPE = -2,      /* unknown key dtype */
+  PDQ_ERR_WORKSPACE = -3,  /* workspace too small or misaligned */
+  PDQ_ERR_CUDA = -4,       /* a CUDA call failed (message has the CUDA error string) */
+  PDQ_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up (persistent segmented path) */
+  PDQ_ERR_INTERNAL = -6    /* a device-side consistency check failed */
+} pdq_status;
+
+typedef struct {
+  int64_t passes;            /* distribution passes (levels) executed over any bucket */
+  int64_t equal_buckets;     /* non-empty equality buckets finished by a splitter (Sec. 3) */
+  int64_t fallback_buckets;  /* buckets sorted by the merge-path fallback (Sec. 4.1) */
+  int64_t reversed;          /* 1 if the input was strictly non-increasing and was reversed */
+  int64_t sorted_exit;       /* 1 if the probe found the input sorted (or all equal) */
+  int64_t learned_overflow;  /* learned path: buckets re-partitioned by the exact repair */
+  int64_t bad_splits;        /* children that kept more than 7/8 of their parent (Sec. 4.1) */
+  int64_t base_buckets;      /* buckets finished by the shared-memory base sort (Sec. 5.1) */
+  int64_t kernel_launches;   /* kernels launched by the call */
+} pdq_stats;
+
+/* Tuning knobs.  Zero in a field means "library default".  Used by tests to force rare paths
+ * (tiny bucket counts and base-case sizes, a zero bad-split budget) on small inputs. */
+typedef struct {
+  int32_t log2_buckets;     /* log2 of buckets per distribution level, 1..10 (default 8) */
+  int32_t oversample;       /* samples per bucket for splitter selection (default 16) */
+  int32_t base_capacity;    /* largest bucket sorted in shared memory, 16..8192, power of 2 */
+  int32_t bad_allowed;      /* >0: start value of the bad-split counter; -1: start at 0 */
+  int32_t probe;            /* 0: default (probe on); -1: skip the sorted/reverse probe */
+  int32_t reserved[3];
+} pdq_tuning;
+
+/* Bytes of workspace the sort of n keys (and a payload of value_bytes, 0 for keys only) needs.
+ * num_segments: 0 or 1 for the single-array calls; the segment count for pdq_sort_segmented.
+ * Returns 0 for an unknown dtype or value_bytes. */
+size_t pdq_workspace_bytes(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes);
+
+/* Sort n keys in place (Sec. 1 problem statement).
+ *   d_keys   : device array of n keys of key_dtype (4- or 8-byte elements, naturally aligned)
+ *   d_ws     : device workspace of ws_bytes >= pdq_workspace_bytes(n, 1, key_dtype, 0)
+ *   tuning   : NULL for defaults                                                          */
+int pdq_sort_keys(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                  void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats);
+
+/* Sort n (key, value) pairs in place by key; values (value_bytes = 4 or 8) move with their key.
+ *   d_vals   : device array of n values                                                   */
+int pdq_sort_pairs(void* d_keys, void* d_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
+                   void* d_ws, size_t ws_bytes, void* cuda_stream, const pdq_tuning* tuning,
+                   pdq_stats* stats);
+
+/* Host-buffer convenience form of pdq_sort_keys / pdq_sort_pairs: copies h_keys (and h_vals
+ * when value_bytes > 0) into the caller's device buffers d_keys / d_vals, sorts them there and
+ * copies the result back into the host arrays, all on cuda_stream; returns after the stream
+ * has finished.  Host arrays should be page-locked for full copy speed. */
+int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
+                  void* d_keys, void* d_vals, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                  const pdq_tuning* tuning, pdq_stats* stats);
+
+/* Reverse n elements of elem_bytes (4 or 8) in place on the device (the descending-input exit
+ * of Sec. 5.2, exposed for testing). */
+int pdq_reverse(void* d_data, int64_t n, int elem_bytes, void* cuda_stream);
+
+/* Message for the last error returned on this host thread ("" if none). */
+const char* pdq_last_error(void);
+
+/* Number of kernels this library has launched in this process (all threads). */
+int64_t pdq_launch_count(void);
+
+/* Per-kernel device time, for measurement: when enabled, each kernel launch of the library is
+ * bracketed by CUDA events on its stream and its time is accumulated per kernel name. */
+void pdq_profile_enable(int on);
+/* Copies up to cap entries: names (each up to 63 chars + NUL, 64 bytes per entry), total
+ * milliseconds, launch counts and the kernels' algorithmic bytes.  Synchronises the device.
+ * Returns the number of kernel names recorded. */
+int pdq_profile_read(char* names, double* total_ms, int64_t* launches, double* bytes, int cap);
+void pdq_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDQ_H_ */

@@ -1,0 +1,221 @@
+"""Python binding of the GB300 pattern-defeating sort library (libpdq.so, C ABI in include/pdq.h).
+
+Argument marshalling only: every step of the sort runs in the library's CUDA kernels.  PyTorch
+provides device memory and streams.  The library must have been built (``__graft_entry__.build()``
+or ``python paper_2106_05123_gb300/_build.py``); there is no CPU fallback, and every call raises
+``PdqError`` when the library or a CUDA device is missing.
+
+Names follow the C ABI: ``pdq_sort_keys``, ``pdq_sort_pairs``, ``pdq_sort_host``,
+``pdq_workspace_bytes``, ``pdq_reverse``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpdq.so")
+
+PDQ_I32, PDQ_U32, PDQ_I64, PDQ_U64, PDQ_F32 = 0, 1, 2, 3, 4
+_STATUS = {0: "PDQ_OK", -1: "PDQ_ERR_ARG", -2: "PDQ_ERR_DTYPE", -3: "PDQ_ERR_WORKSPACE",
+           -4: "PDQ_ERR_CUDA", -5: "PDQ_ERR_TIMEOUT", -6: "PDQ_ERR_INTERNAL"}
+
+_TORCH_DT = {
+    torch.int32: PDQ_I32,
+    torch.int64: PDQ_I64,
+    torch.float32: PDQ_F32,
+}
+if hasattr(torch, "uint32"):
+    _TORCH_DT[torch.uint32] = PDQ_U32
+if hasattr(torch, "uint64"):
+    _TORCH_DT[torch.uint64] = PDQ_U64
+
+
+class PdqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "passes", "equal_buckets", "fallback_buckets", "reversed", "sorted_exit",
+        "learned_overflow", "bad_splits", "base_buckets", "kernel_launches")]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("log2_buckets", ctypes.c_int32), ("oversample", ctypes.c_int32),
+                ("base_capacity", ctypes.c_int32), ("bad_allowed", ctypes.c_int32),
+                ("probe", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpdq.so (raises PdqError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise PdqError(-4, f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+            P = ctypes.POINTER
+            L.pdq_workspace_bytes.argtypes = [i64, i64, i32, i32]
+            L.pdq_workspace_bytes.restype = sz
+            L.pdq_sort_keys.argtypes = [vp, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_keys.restype = i32
+            L.pdq_sort_pairs.argtypes = [vp, vp, i32, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_pairs.restype = i32
+            L.pdq_sort_host.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_host.restype = i32
+            L.pdq_reverse.argtypes = [vp, i64, i32, vp]
+            L.pdq_reverse.restype = i32
+            L.pdq_last_error.argtypes = []
+            L.pdq_last_error.restype = ctypes.c_char_p
+            L.pdq_launch_count.argtypes = []
+            L.pdq_launch_count.restype = i64
+            L.pdq_profile_enable.argtypes = [i32]
+            L.pdq_profile_enable.restype = None
+            L.pdq_profile_read.argtypes = [ctypes.c_char_p, P(ctypes.c_double), P(i64),
+                                           P(ctypes.c_double), i32]
+            L.pdq_profile_read.restype = i32
+            L.pdq_profile_reset.argtypes = []
+            L.pdq_profile_reset.restype = None
+            _lib = L
+        return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise PdqError(rc, lib().pdq_last_error().decode())
+
+
+def key_dtype_code(t: torch.dtype) -> int:
+    if t not in _TORCH_DT:
+        raise PdqError(-2, f"unsupported key dtype {t}")
+    return _TORCH_DT[t]
+
+
+def _stream_ptr(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _tuning(t) -> ctypes.POINTER(Tuning) | None:
+    if t is None:
+        return None
+    if isinstance(t, Tuning):
+        return ctypes.pointer(t)
+    tt = Tuning()
+    for k, v in dict(t).items():
+        setattr(tt, k, int(v))
+    return ctypes.pointer(tt)
+
+
+def pdq_workspace_bytes(n: int, key_dtype, value_bytes: int = 0, num_segments: int = 1) -> int:
+    """Workspace bytes for a call; key_dtype is a torch dtype or a PDQ_* code."""
+    code = key_dtype if isinstance(key_dtype, int) else key_dtype_code(key_dtype)
+    return int(lib().pdq_workspace_bytes(int(n), int(num_segments), code, int(value_bytes)))
+
+
+def workspace_for(n: int, key_dtype: torch.dtype, value_bytes: int = 0, num_segments: int = 1,
+                  device="cuda") -> torch.Tensor:
+    """A uint8 device tensor large enough (and 256-byte aligned) for the call."""
+    nbytes = pdq_workspace_bytes(n, key_dtype, value_bytes, num_segments)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def _require_cuda(t: torch.Tensor, what: str) -> None:
+    if not t.is_cuda:
+        raise PdqError(-1, f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise PdqError(-1, f"{what} must be contiguous")
+
+
+def pdq_sort_keys(keys: torch.Tensor, workspace: torch.Tensor | None = None, tuning=None,
+                  stream=None, key_dtype: int | None = None) -> dict:
+    """Sort a 1-D CUDA tensor in place (ascending; float32 in IEEE totalOrder).  ``key_dtype``
+    (a PDQ_* code) overrides the tensor's dtype, e.g. to sort an int32 view as uint32."""
+    _require_cuda(keys, "keys")
+    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    n = keys.numel()
+    ws = workspace if workspace is not None else workspace_for(n, keys.dtype, 0, 1, keys.device)
+    st = Stats()
+    _check(lib().pdq_sort_keys(keys.data_ptr(), n, dt, ws.data_ptr(), ws.numel(),
+                               _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, workspace: torch.Tensor | None = None,
+                   tuning=None, stream=None, key_dtype: int | None = None) -> dict:
+    """Sort (key, value) pairs in place by key; values (4- or 8-byte elements) follow keys."""
+    _require_cuda(keys, "keys")
+    _require_cuda(vals, "vals")
+    if vals.numel() != keys.numel():
+        raise PdqError(-1, "keys and vals differ in length")
+    vb = vals.element_size()
+    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    n = keys.numel()
+    ws = workspace if workspace is not None else workspace_for(n, keys.dtype, vb, 1, keys.device)
+    st = Stats()
+    _check(lib().pdq_sort_pairs(keys.data_ptr(), vals.data_ptr(), vb, n, dt, ws.data_ptr(),
+                                ws.numel(), _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_sort_host(h_keys: torch.Tensor, d_keys: torch.Tensor, workspace: torch.Tensor,
+                  h_vals: torch.Tensor | None = None, d_vals: torch.Tensor | None = None,
+                  tuning=None, stream=None) -> dict:
+    """Sort host tensors through caller-provided device buffers (copies in, sorts, copies out)."""
+    if h_keys.is_cuda or not d_keys.is_cuda:
+        raise PdqError(-1, "h_keys must be a host tensor and d_keys a CUDA tensor")
+    dt = key_dtype_code(h_keys.dtype)
+    vb = h_vals.element_size() if h_vals is not None else 0
+    st = Stats()
+    _check(lib().pdq_sort_host(h_keys.data_ptr(), h_vals.data_ptr() if h_vals is not None else None,
+                               vb, h_keys.numel(), dt, d_keys.data_ptr(),
+                               d_vals.data_ptr() if d_vals is not None else None,
+                               workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
+                               _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_reverse(t: torch.Tensor, stream=None) -> None:
+    _require_cuda(t, "t")
+    _check(lib().pdq_reverse(t.data_ptr(), t.numel(), t.element_size(), _stream_ptr(stream)))
+
+
+def launch_count() -> int:
+    return int(lib().pdq_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().pdq_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    lib().pdq_profile_reset()
+
+
+def profile_read(cap: int = 64) -> dict:
+    """Per-kernel {name: (total_ms, launches, algorithmic_bytes)} since the last reset."""
+    names = ctypes.create_string_buffer(64 * cap)
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int64 * cap)()
+    by = (ctypes.c_double * cap)()
+    k = min(cap, lib().pdq_profile_read(names, ms, cnt, by, cap))
+    out = {}
+    for i in range(k):
+        nm = names.raw[64 * i:64 * i + 64].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[i], int(cnt[i]), by[i])
+    return out

@@ -1,0 +1,277 @@
+// C ABI of the library (see include/pdq.h): argument checks, dtype dispatch, error strings,
+// launch counting and the optional per-kernel event timing used for measurement.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "sort_api.h"
+
+namespace pdq {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+// ------------------------------------------------------------------ launch accounting
+static std::atomic<int64_t> g_launches{0};
+static std::atomic<bool> g_profile{false};
+
+struct ProfEntry {
+  double ms = 0.0;
+  int64_t launches = 0;
+  double bytes = 0.0;
+};
+struct Pending {
+  std::string name;
+  cudaEvent_t e0, e1;
+  double bytes;
+};
+static std::mutex g_prof_mu;
+static std::map<std::string, ProfEntry> g_prof;
+static std::vector<Pending> g_pending;
+static thread_local std::vector<Pending> t_open;
+
+void note_launch(const char* name, cudaStream_t s, double bytes) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_profile.load(std::memory_order_relaxed)) return;
+  Pending p;
+  p.name = name;
+  p.bytes = bytes;
+  cudaEventCreate(&p.e0);
+  cudaEventCreate(&p.e1);
+  cudaEventRecord(p.e0, s);
+  t_open.push_back(p);
+}
+
+void note_launch_end(const char* name, cudaStream_t s) {
+  if (t_open.empty()) return;
+  Pending p = t_open.back();
+  t_open.pop_back();
+  (void)name;
+  cudaEventRecord(p.e1, s);
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_pending.push_back(p);
+}
+
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+static void resolve_pending() {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (Pending& p : g_pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.e1);
+    cudaEventElapsedTime(&ms, p.e0, p.e1);
+    ProfEntry& e = g_prof[p.name];
+    e.ms += ms;
+    e.launches += 1;
+    e.bytes += p.bytes;
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  g_pending.clear();
+}
+
+// ------------------------------------------------------------------ dispatch helpers
+static int key_bytes(int dt) {
+  switch (dt) {
+    case PDQ_I32: case PDQ_U32: case PDQ_F32: return 4;
+    case PDQ_I64: case PDQ_U64: return 8;
+    default: return 0;
+  }
+}
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 148;
+  }
+  return sms;
+}
+
+static int make_tuning(const pdq_tuning* t, Tuning* out) {
+  Tuning d;
+  d.logb = kDefaultLogB;
+  d.oversample = kDefaultOversample;
+  d.base_cap = kBaseCapMax;
+  d.bad_allowed = 0;
+  d.probe = true;
+  if (t) {
+    if (t->log2_buckets) {
+      if (t->log2_buckets < 1 || t->log2_buckets > kLogBMax)
+        return set_error(PDQ_ERR_ARG, "tuning.log2_buckets out of range 1..10");
+      d.logb = t->log2_buckets;
+    }
+    if (t->oversample) {
+      if (t->oversample < 1 || t->oversample > kMaxSamples || (t->oversample & (t->oversample - 1)))
+        return set_error(PDQ_ERR_ARG, "tuning.oversample must be a power of two <= 4096");
+      d.oversample = t->oversample;
+    }
+    if (t->base_capacity) {
+      const int c = t->base_capacity;
+      if (c < kBaseCapMin || c > kBaseCapMax || (c & (c - 1)))
+        return set_error(PDQ_ERR_ARG, "tuning.base_capacity must be a power of two in 256..8192");
+      d.base_cap = c;
+    }
+    if (t->bad_allowed) d.bad_allowed = t->bad_allowed;
+    if (t->probe < 0) d.probe = false;
+  }
+  *out = d;
+  return PDQ_OK;
+}
+
+template <int VB>
+static int dispatch_sort(int dt, const SortArgs& a, pdq_stats* st) {
+  switch (dt) {
+    case PDQ_I32: return sort_impl<PDQ_I32, VB>(a, st);
+    case PDQ_U32: return sort_impl<PDQ_U32, VB>(a, st);
+    case PDQ_I64: return sort_impl<PDQ_I64, VB>(a, st);
+    case PDQ_U64: return sort_impl<PDQ_U64, VB>(a, st);
+    case PDQ_F32: return sort_impl<PDQ_F32, VB>(a, st);
+    default: return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  }
+}
+
+template <int VB>
+static size_t dispatch_ws(int dt, int64_t n) {
+  switch (dt) {
+    case PDQ_I32: return workspace_bytes_impl<PDQ_I32, VB>(n);
+    case PDQ_U32: return workspace_bytes_impl<PDQ_U32, VB>(n);
+    case PDQ_I64: return workspace_bytes_impl<PDQ_I64, VB>(n);
+    case PDQ_U64: return workspace_bytes_impl<PDQ_U64, VB>(n);
+    case PDQ_F32: return workspace_bytes_impl<PDQ_F32, VB>(n);
+    default: return 0;
+  }
+}
+
+static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int dt, void* ws,
+                       size_t ws_bytes, void* stream, const pdq_tuning* tuning, pdq_stats* stats) {
+  g_last_error.clear();
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int kb = key_bytes(dt);
+  if (!kb) return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  if (n < 0 || n >= (int64_t(1) << 32)) return set_error(PDQ_ERR_ARG, "n must be in [0, 2^32)");
+  if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8)
+    return set_error(PDQ_ERR_ARG, "value_bytes must be 4 or 8");
+  if (n <= 1) return PDQ_OK;
+  if (!keys || ((uintptr_t)keys % kb)) return set_error(PDQ_ERR_ARG, "keys pointer null or misaligned");
+  if (value_bytes && (!vals || ((uintptr_t)vals % value_bytes)))
+    return set_error(PDQ_ERR_ARG, "values pointer null or misaligned");
+  if (!ws || ((uintptr_t)ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
+  SortArgs a;
+  a.keys = keys;
+  a.vals = vals;
+  a.n = n;
+  a.ws = ws;
+  a.ws_bytes = ws_bytes;
+  a.stream = static_cast<cudaStream_t>(stream);
+  a.num_sms = num_sms();
+  int rc = make_tuning(tuning, &a.tune);
+  if (rc) return rc;
+  switch (value_bytes) {
+    case 0: return dispatch_sort<0>(dt, a, stats);
+    case 4: return dispatch_sort<4>(dt, a, stats);
+    default: return dispatch_sort<8>(dt, a, stats);
+  }
+}
+
+}  // namespace pdq
+
+using namespace pdq;
+
+extern "C" {
+
+size_t pdq_workspace_bytes(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes) {
+  (void)num_segments;
+  if (n < 0) return 0;
+  switch (value_bytes) {
+    case 0: return dispatch_ws<0>(key_dtype, n);
+    case 4: return dispatch_ws<4>(key_dtype, n);
+    case 8: return dispatch_ws<8>(key_dtype, n);
+    default: return 0;
+  }
+}
+
+int pdq_sort_keys(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                  void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats) {
+  return sort_common(d_keys, nullptr, 0, n, key_dtype, d_ws, ws_bytes, cuda_stream, tuning, stats);
+}
+
+int pdq_sort_pairs(void* d_keys, void* d_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
+                   void* d_ws, size_t ws_bytes, void* cuda_stream, const pdq_tuning* tuning,
+                   pdq_stats* stats) {
+  if (value_bytes != 4 && value_bytes != 8) return set_error(PDQ_ERR_ARG, "value_bytes must be 4 or 8");
+  return sort_common(d_keys, d_vals, value_bytes, n, key_dtype, d_ws, ws_bytes, cuda_stream, tuning, stats);
+}
+
+int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
+                  void* d_keys, void* d_vals, void* d_ws, size_t ws_bytes, void* cuda_stream,
+                  const pdq_tuning* tuning, pdq_stats* stats) {
+  g_last_error.clear();
+  const int kb = key_bytes(key_dtype);
+  if (!kb) return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  if (n < 0) return set_error(PDQ_ERR_ARG, "n must be >= 0");
+  if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8)
+    return set_error(PDQ_ERR_ARG, "value_bytes must be 0, 4 or 8");
+  if (n == 0) return PDQ_OK;
+  if (!h_keys || !d_keys || (value_bytes && (!h_vals || !d_vals)))
+    return set_error(PDQ_ERR_ARG, "null buffer");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaMemcpyAsync(d_keys, h_keys, (size_t)n * kb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && value_bytes)
+    e = cudaMemcpyAsync(d_vals, h_vals, (size_t)n * value_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("H2D: ") + cudaGetErrorString(e));
+  int rc = sort_common(d_keys, d_vals, value_bytes, n, key_dtype, d_ws, ws_bytes, cuda_stream, tuning, stats);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(h_keys, d_keys, (size_t)n * kb, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && value_bytes)
+    e = cudaMemcpyAsync(h_vals, d_vals, (size_t)n * value_bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("D2H: ") + cudaGetErrorString(e));
+  return PDQ_OK;
+}
+
+const char* pdq_last_error(void) { return g_last_error.c_str(); }
+
+int64_t pdq_launch_count(void) { return launches_so_far(); }
+
+void pdq_profile_enable(int on) { g_profile.store(on != 0); }
+
+int pdq_profile_read(char* names, double* total_ms, int64_t* launches, double* bytes, int cap) {
+  cudaDeviceSynchronize();
+  resolve_pending();
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  int i = 0;
+  for (const auto& kv : g_prof) {
+    if (i >= cap) break;
+    if (names) {
+      std::strncpy(names + 64 * i, kv.first.c_str(), 63);
+      names[64 * i + 63] = 0;
+    }
+    if (total_ms) total_ms[i] = kv.second.ms;
+    if (launches) launches[i] = kv.second.launches;
+    if (bytes) bytes[i] = kv.second.bytes;
+    ++i;
+  }
+  return (int)g_prof.size();
+}
+
+void pdq_profile_reset(void) {
+  cudaDeviceSynchronize();
+  resolve_pending();
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  g_prof.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Internal interface between the C ABI (api.cu) and the per-dtype sort instantiations.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pdq.h"
+
+namespace pdq {
+
+struct Tuning {
+  int logb;          // log2 of the largest bucket count per level
+  int oversample;    // samples per bucket (power of two)
+  int base_cap;      // largest bucket for the shared-memory base sort (power of two)
+  int bad_allowed;   // >0 forced start of the bad-split counter, -1 start at 0, 0 floor(log2 n)
+  bool probe;        // run the sorted / reverse probe
+};
+
+struct SortArgs {
+  void* keys;
+  void* vals;
+  int64_t n;
+  void* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+  Tuning tune;
+  int num_sms;
+};
+
+// Byte offsets of the workspace regions.
+struct Layout {
+  size_t tmpk, tmpv, ctr, tasks_cur, tasks_next, task_meta, chunks, counts, tree, spl, children,
+      base_items, copy_items, fb_items, total;
+  int64_t task_cap, round_cap, chunk_cap, item_cap;
+};
+
+int set_error(int code, const std::string& msg);
+
+template <int KT, int VB>
+int sort_impl(const SortArgs& a, pdq_stats* stats);
+template <int KT, int VB>
+size_t workspace_bytes_impl(int64_t n);
+
+}  // namespace pdq

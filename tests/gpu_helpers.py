@@ -1,0 +1,48 @@
+"""Helpers shared by the GPU tests: run the CUDA path through the C ABI on numpy inputs."""
+
+import numpy as np
+import torch
+
+import paper_2106_05123_gb300 as pdq
+
+CODE = {
+    np.dtype(np.int32): pdq.PDQ_I32,
+    np.dtype(np.uint32): pdq.PDQ_U32,
+    np.dtype(np.int64): pdq.PDQ_I64,
+    np.dtype(np.uint64): pdq.PDQ_U64,
+    np.dtype(np.float32): pdq.PDQ_F32,
+}
+# transport dtypes: unsigned keys travel as same-width signed tensors (the ABI takes raw bits)
+CARRIER = {4: (np.int32, torch.int32), 8: (np.int64, torch.int64)}
+
+
+def to_device(a: np.ndarray) -> torch.Tensor:
+    npdt, _ = CARRIER[a.dtype.itemsize]
+    if a.dtype == np.float32:
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a).view(npdt)).cuda()
+
+
+def to_host(t: torch.Tensor, dtype) -> np.ndarray:
+    return t.cpu().numpy().view(dtype)
+
+
+def gpu_sort(keys: np.ndarray, vals: np.ndarray | None = None, tuning=None):
+    """Sort keys (and values) with the CUDA path; returns (keys, vals, stats) as numpy."""
+    code = CODE[keys.dtype]
+    dk = to_device(keys)
+    n = keys.size
+    vb = vals.dtype.itemsize if vals is not None else 0
+    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb)), dtype=torch.uint8, device="cuda")
+    if vals is None:
+        st = pdq.pdq_sort_keys(dk, workspace=ws, tuning=tuning, key_dtype=code)
+        torch.cuda.synchronize()
+        return to_host(dk, keys.dtype), None, st
+    dv = to_device(vals)
+    st = pdq.pdq_sort_pairs(dk, dv, workspace=ws, tuning=tuning, key_dtype=code)
+    torch.cuda.synchronize()
+    return to_host(dk, keys.dtype), to_host(dv, vals.dtype), st
+
+
+def bits(a: np.ndarray) -> np.ndarray:
+    return a.view({4: np.uint32, 8: np.uint64}[a.dtype.itemsize])

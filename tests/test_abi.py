@@ -1,0 +1,69 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/pdq.h
+declares; host-side argument checks answer without a GPU (no compute calls here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pdq.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2106_05123_gb300 import _build
+    _build.build()
+    import paper_2106_05123_gb300 as pdq
+    return pdq.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdq_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("pdq_sort_keys", "pdq_sort_pairs", "pdq_workspace_bytes", "pdq_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_workspace_bytes_is_host_logic(L):
+    import paper_2106_05123_gb300 as pdq
+    small = pdq.pdq_workspace_bytes(1000, pdq.PDQ_I32, 0)
+    big = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_I32, 0)
+    pairs = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_I32, 4)
+    wide = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_U64, 0)
+    assert 0 < small < big < pairs and big < wide
+    assert big >= 4 * (1 << 20)          # at least the temp key buffer
+    assert pdq.pdq_workspace_bytes(10, 7, 0) == 0       # unknown dtype
+    assert pdq.pdq_workspace_bytes(10, pdq.PDQ_I32, 3) == 0
+
+
+def test_argument_errors_need_no_device(L):
+    import paper_2106_05123_gb300 as pdq
+    st = pdq.Stats()
+    # unknown dtype, bad value width, n out of range, null pointers: rejected before any CUDA call
+    assert L.pdq_sort_keys(None, 10, 9, None, 0, None, None, ctypes.byref(st)) == -2
+    assert L.pdq_sort_pairs(None, None, 3, 10, 0, None, 0, None, None, ctypes.byref(st)) == -1
+    assert L.pdq_sort_keys(None, 1 << 33, 0, None, 0, None, None, ctypes.byref(st)) == -1
+    assert L.pdq_sort_keys(None, 10, 0, None, 0, None, None, ctypes.byref(st)) == -1
+    assert b"keys" in L.pdq_last_error()
+    # n = 0 / 1 are no-ops
+    assert L.pdq_sort_keys(None, 0, 0, None, 0, None, None, ctypes.byref(st)) == 0
+    assert L.pdq_sort_keys(None, 1, 0, None, 0, None, None, ctypes.byref(st)) == 0
+    # misaligned workspace
+    assert L.pdq_sort_keys(ctypes.c_void_p(4096), 10, 0, ctypes.c_void_p(4100), 1 << 20, None, None,
+                           ctypes.byref(st)) == -3
+    # bad tuning values
+    bad = pdq.Tuning(log2_buckets=11)
+    assert L.pdq_sort_keys(ctypes.c_void_p(4096), 10, 0, ctypes.c_void_p(4096), 1 << 20, None,
+                           ctypes.byref(bad), ctypes.byref(st)) in (-1, -3)

@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, bit for bit.
+
+Keys must equal the oracle's output exactly (the sorted arrangement is unique under numeric
+order and IEEE totalOrder).  For pairs, several outputs are correct (values inside a run of
+equal keys are unordered, Sec. 1): keys must match exactly and every value must sit with its
+own key, each exactly once.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_helpers import bits, gpu_sort
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [np.int32, np.uint32, np.int64, np.uint64, np.float32]
+SIZES = [0, 1, 2, 3, 31, 32, 33, 255, 256, 257, 8191, 8192, 8193, 8194, 65537, 300001]
+
+
+def oracle_sorted(a):
+    b = a.copy()
+    oracle.pdqsort(b)
+    return b
+
+
+def keys_for(dtype, n, seed):
+    if dtype == np.float32:
+        k, _ = workloads.normal_f32_specials(n, seed, frac=0.01)
+        return k
+    return workloads.uniform_bits(n, dtype, seed)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", SIZES)
+def test_keys_random(dtype, n):
+    a = keys_for(dtype, n, workloads.substream(1, n))
+    got, _, _ = gpu_sort(a)
+    assert np.array_equal(bits(got), bits(oracle_sorted(a)))
+
+
+@pytest.mark.parametrize("name", workloads.SWEEP_PATTERNS + ["dupsq", "dup8", "mod8", "sort50",
+                                                             "sort90", "sort99", "merge", "random"])
+@pytest.mark.parametrize("n", [1 << 14, 100003, 1 << 20])
+def test_patterns_int32(name, n):
+    a = workloads.pattern(name, n, 7, dtype=np.int32)
+    got, _, st = gpu_sort(a)
+    assert np.array_equal(got, oracle_sorted(a))
+
+
+TUNINGS = [
+    dict(log2_buckets=1, base_capacity=256),                # two-way splits: many levels
+    dict(log2_buckets=2, oversample=1, base_capacity=256),  # poor samples: bad splits likely
+    dict(log2_buckets=3, base_capacity=512),
+    dict(log2_buckets=10, base_capacity=256),               # widest level
+    dict(bad_allowed=-1, base_capacity=256),                # counter starts at 0: fallback only
+    dict(bad_allowed=1, log2_buckets=1, oversample=1, base_capacity=256),  # early fallback
+    dict(probe=-1),
+]
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=[str(i) for i in range(len(TUNINGS))])
+@pytest.mark.parametrize("dtype", [np.int32, np.uint64, np.float32])
+@pytest.mark.parametrize("name", ["random", "mod8", "organ", "dupsq", "sawtooth"])
+def test_knobs_force_rare_paths(tuning, dtype, name):
+    n = 40000
+    if name == "random":
+        a = keys_for(dtype, n, 5)
+    else:
+        a = workloads.pattern(name, n, 5, dtype=np.int64).astype(dtype)
+    got, _, st = gpu_sort(a, tuning=tuning)
+    assert np.array_equal(bits(got), bits(oracle_sorted(a)))
+    if tuning.get("bad_allowed") == -1:
+        assert st["fallback_buckets"] >= 1
+
+
+@pytest.mark.parametrize("vdtype", [np.uint32, np.uint64])
+@pytest.mark.parametrize("kdtype", DTYPES)
+@pytest.mark.parametrize("n", [5, 8193, 200001])
+def test_pairs_values_stay_attached(kdtype, vdtype, n):
+    if kdtype == np.float32:
+        keys, _ = workloads.normal_f32_specials(n, 3, frac=0.01)
+    else:
+        keys = (workloads.splitmix64(3, n) % np.uint64(997)).astype(kdtype)  # many ties
+    vals = np.arange(n, dtype=vdtype)
+    gk, gv, _ = gpu_sort(keys, vals)
+    ok, ov = keys.copy(), vals.copy()
+    oracle.pdqsort_pairs(ok, ov)
+    assert np.array_equal(bits(gk), bits(ok))
+    idx = gv.astype(np.int64)
+    assert np.array_equal(np.sort(idx), np.arange(n))          # a permutation of the values
+    assert np.array_equal(bits(keys[idx]), bits(gk))           # each value with its own key
+
+
+@pytest.mark.parametrize("tuning", [None, dict(bad_allowed=-1, base_capacity=256),
+                                    dict(log2_buckets=1, base_capacity=256)])
+def test_pairs_through_fallback_and_levels(tuning):
+    n = 100000
+    keys = workloads.pattern("dupsq", n, 9, dtype=np.int32)
+    vals = np.arange(n, dtype=np.uint32)
+    gk, gv, _ = gpu_sort(keys, vals, tuning=tuning)
+    assert np.array_equal(gk, np.sort(keys))
+    assert np.array_equal(keys[gv.astype(np.int64)], gk)
+    assert np.array_equal(np.sort(gv), vals)
+
+
+def test_float_golden_total_order():
+    import os
+    words = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "float32_total_order.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                words.append(int(line, 16))
+    want = np.array(words, dtype=np.uint32)
+    big = np.tile(want, 2000)[workloads.permutation(want.size * 2000, 4)]
+    got, _, _ = gpu_sort(big.view(np.float32).copy())
+    assert np.array_equal(bits(got), np.repeat(want, 2000))
+
+
+# ------------------------------------------------------------------- heuristics (stats)
+def test_sorted_exit_and_reverse():
+    n = 1 << 20
+    asc = np.arange(n, dtype=np.int32)
+    got, _, st = gpu_sort(asc)
+    assert np.array_equal(got, asc) and st["sorted_exit"] == 1 and st["passes"] == 0
+    desc = asc[::-1].copy()
+    got, _, st = gpu_sort(desc)
+    assert np.array_equal(got, asc) and st["reversed"] == 1 and st["passes"] == 0
+    ones = np.ones(n, dtype=np.int32)
+    got, _, st = gpu_sort(ones)
+    assert st["sorted_exit"] == 1 and st["passes"] == 0
+    # non-increasing with equal runs is reversed too (unstable order is allowed)
+    steps = (np.arange(n)[::-1] // 7).astype(np.int32)
+    got, _, st = gpu_sort(steps)
+    assert np.array_equal(got, np.sort(steps)) and st["reversed"] == 1
+
+
+def test_equal_keys_are_final_after_one_level():
+    """The equal-key rule (Sec. 3): with k = 16 distinct keys every key lands in an equality
+    bucket on the first level, so one distribution pass finishes the sort (O(nk), Theorem 1)."""
+    n = 1 << 20
+    a = workloads.pattern("mod16", n, 2, dtype=np.int32)
+    got, _, st = gpu_sort(a)
+    assert np.array_equal(got, np.sort(a))
+    assert st["passes"] == 1 and st["equal_buckets"] == 16 and st["base_buckets"] == 0
+
+
+@pytest.mark.parametrize("k", [2, 3, 5, 40])
+def test_few_distinct_passes_bounded(k):
+    n = 300000
+    a = (workloads.splitmix64(11, n) % np.uint64(k)).astype(np.int64) * 1000003
+    got, _, st = gpu_sort(a, tuning=dict(log2_buckets=1, base_capacity=256))
+    assert np.array_equal(got, np.sort(a))
+    assert st["passes"] <= k
+
+
+def test_fallback_when_budget_is_zero():
+    n = 50000
+    a = workloads.pattern("random", n, 8, dtype=np.int32)
+    got, _, st = gpu_sort(a, tuning=dict(bad_allowed=-1, base_capacity=256))
+    assert np.array_equal(got, np.sort(a))
+    assert st["fallback_buckets"] == 1 and st["passes"] == 0
