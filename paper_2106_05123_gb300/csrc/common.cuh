@@ -56,6 +56,8 @@ struct Counters {
   unsigned long long equal_buckets;
   unsigned long long bad_splits;
   unsigned long long overflow;      // a list would have exceeded its capacity
+  unsigned long long base_elems;    // elements in the base-sort list
+  unsigned long long copy_elems;    // elements in the copy list
   unsigned long long probe[8];      // probe results: descents, ascents, min code, max code
 };
 

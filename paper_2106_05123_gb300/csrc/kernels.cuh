@@ -417,11 +417,15 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   };
   if (b & 1) {  // equality bucket: every key equals the splitter, final (Sec. 3)
     atomicAdd(&ctr->equal_buckets, 1ull);
-    if (dst == kBufTmp) push(copy_items, &ctr->n_copy);
+    if (dst == kBufTmp) {
+      push(copy_items, &ctr->n_copy);
+      atomicAdd(&ctr->copy_elems, (unsigned long long)ch.y);
+    }
     return;
   }
   if ((int64_t)ch.y <= base_cap) {
     push(base_items, &ctr->n_base[0]);
+    atomicAdd(&ctr->base_elems, (unsigned long long)ch.y);
     return;
   }
   // bad split: the child kept more than 7/8 of its parent (p = 1/8, a shift; Sec. 4.1)

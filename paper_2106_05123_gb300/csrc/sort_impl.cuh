@@ -119,7 +119,7 @@ class PlainSorter {
     if (n <= cap) {
       Item it{0, (uint32_t)n, kBufKeys, 0};
       PDQ_CUDA(cudaMemcpyAsync(base_items_, &it, sizeof(it), cudaMemcpyHostToDevice, st_));
-      return base_sort(1, kBufKeys, 1);
+      return base_sort(1, kBufKeys, 1, n);
     }
     if (a_.tune.probe) {
       bool done = false;
@@ -306,11 +306,11 @@ class PlainSorter {
     stats_.equal_buckets += (int64_t)h.equal_buckets;
     stats_.bad_splits += (int64_t)h.bad_splits;
     if (h.n_base[0]) {
-      int rc = base_sort((int64_t)h.n_base[0], kBufKeys, 1);
+      int rc = base_sort((int64_t)h.n_base[0], kBufKeys, 1, (int64_t)h.base_elems);
       if (rc) return rc;
     }
     if (h.n_copy) {
-      LaunchScope ls("copy", st_, 0.0);
+      LaunchScope ls("copy", st_, 2.0 * (double)h.copy_elems * (KS + VB));
       dim3 grid((unsigned)h.n_copy, 16);
       copy_kernel<KT, VB><<<grid, 256, 0, st_>>>(copy_items_, keys_, vals_, tmpk_, tmpv_);
     }
@@ -334,13 +334,13 @@ class PlainSorter {
     return PDQ_OK;
   }
 
-  // Base sort of `count` items already in base_items_.
-  int base_sort(int64_t count, int out_buf, int decode) {
+  // Base sort of `count` items (holding `elems` elements) already in base_items_.
+  int base_sort(int64_t count, int out_buf, int decode, int64_t elems) {
     const int cap = a_.tune.base_cap;
     stats_.base_buckets += count;
     for (int64_t done = 0; done < count;) {
       const int64_t g = std::min<int64_t>(count - done, 1 << 30);
-      LaunchScope ls("base_sort", st_, 0.0);
+      LaunchScope ls("base_sort", st_, done == 0 ? 2.0 * (double)elems * (KS + VB) : 0.0);
       base_sort_kernel<KT, VB, S::kBaseThreads><<<(unsigned)g, S::kBaseThreads, S::base_smem(cap), st_>>>(
           base_items_ + done, cap, keys_, vals_, tmpk_, tmpv_, out_buf, decode);
       done += g;
@@ -367,7 +367,8 @@ class PlainSorter {
         tiles.push_back(Item{it.begin + b, (uint32_t)std::min<int64_t>(run, (int64_t)it.size - b), it.buf, it.enc});
       }
       PDQ_CUDA(cudaMemcpyAsync(base_items_, tiles.data(), sizeof(Item) * tiles.size(), cudaMemcpyHostToDevice, st_));
-      int rc = base_sort((int64_t)tiles.size(), x, passes == 0 ? 1 : 0);
+      const int64_t tile_elems = std::min<int64_t>((int64_t)it.size - t0 * run, (t1 - t0) * run);
+      int rc = base_sort((int64_t)tiles.size(), x, passes == 0 ? 1 : 0, tile_elems);
       if (rc) return rc;
       stats_.base_buckets -= (int64_t)tiles.size();  // tiles are not buckets
       PDQ_CUDA(cudaStreamSynchronize(st_));  // tiles buffer is reused by the next batch
