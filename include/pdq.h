@@ -106,6 +106,18 @@ int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dt
                   void* d_keys, void* d_vals, void* d_ws, size_t ws_bytes, void* cuda_stream,
                   const pdq_tuning* tuning, pdq_stats* stats);
 
+/* Keys-only sort that allocates nothing, for callers that cannot call cudaMalloc (code whose
+ * device memory is owned by a framework's allocator, fixed-budget plug-ins, latency-sensitive
+ * loops where cudaMalloc/cudaFree would synchronise the device).  The paper has no counterpart:
+ * this is a memory-ownership variant of pdq_sort_keys.  Its scratch is one file-scope device
+ * array of 64 MiB per GPU, held until the process exits; it covers up to 2^20 keys of any key
+ * type, and larger n returns PDQ_ERR_ARG with the limit in the message.  The first call on a
+ * device (with that device current) looks up the array's device address; make that first call
+ * before any stream capture.  All calls on a device share the array: calls that overlap on the
+ * GPU race and must not be issued.  d_keys, n, key_dtype, cuda_stream, stats: as pdq_sort_keys. */
+int pdq_sort_keys_noalloc(void* d_keys, int64_t n, pdq_dtype key_dtype, void* cuda_stream,
+                          pdq_stats* stats);
+
 /* Reverse n elements of elem_bytes (4 or 8) in place on the device (the descending-input exit
  * of Sec. 5.2, exposed for testing). */
 int pdq_reverse(void* d_data, int64_t n, int elem_bytes, void* cuda_stream);

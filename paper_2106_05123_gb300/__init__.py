@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
             L.pdq_sort_pairs.restype = i32
             L.pdq_sort_host.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, sz, vp, P(Tuning), P(Stats)]
             L.pdq_sort_host.restype = i32
+            L.pdq_sort_keys_noalloc.argtypes = [vp, i64, i32, vp, P(Stats)]
+            L.pdq_sort_keys_noalloc.restype = i32
             L.pdq_reverse.argtypes = [vp, i64, i32, vp]
             L.pdq_reverse.restype = i32
             L.pdq_last_error.argtypes = []
@@ -187,6 +189,17 @@ def pdq_sort_host(h_keys: torch.Tensor, d_keys: torch.Tensor, workspace: torch.T
                                d_vals.data_ptr() if d_vals is not None else None,
                                workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
                                _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_sort_keys_noalloc(keys: torch.Tensor, stream=None, key_dtype: int | None = None) -> dict:
+    """Keys-only sort that allocates nothing: its scratch is the library's fixed 64 MiB device
+    array (n <= 2^20).  For callers that cannot allocate device memory."""
+    _require_cuda(keys, "keys")
+    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    st = Stats()
+    _check(lib().pdq_sort_keys_noalloc(keys.data_ptr(), keys.numel(), dt, _stream_ptr(stream),
+                                       ctypes.byref(st)))
     return st.as_dict()
 
 
