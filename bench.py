@@ -44,6 +44,7 @@ WORKLOADS = {
     # name: (description, n, key dtype, value dtype or None)
     "uniform_i32_2p28": ("uniform int32 keys, n=2^28", 1 << 28, np.int32, None),
     "uniform_i32_2p20": ("uniform int32 keys, n=2^20", 1 << 20, np.int32, None),
+    "uniform_i32_2p26": ("uniform int32 keys, n=2^26 (profiling size)", 1 << 26, np.int32, None),
     "sweep_i32_2p24": ("pattern sweep, 8 int32 patterns of n=2^24 each per step", 1 << 24, np.int32, None),
     "pairs_u64_zipf_2p27": ("uint64 Zipf(1.1) keys over 256 values + uint32 index, n=2^27", 1 << 27,
                             np.uint64, np.uint32),

@@ -30,6 +30,8 @@
  *     256-byte aligned.  The library allocates no device memory of its own, except the
  *     segmented path's CUDA-graph cache (see pdq_sort_segmented).
  *   - n must be < 2^32.  n = 0 and n = 1 are no-ops.  value_bytes is 4 or 8.
+ *   - d_keys and d_vals must be 16-byte aligned (tiles are staged by bulk copies); any
+ *     allocation from cudaMalloc or PyTorch's allocator is.
  *   - Return value: PDQ_OK or a negative pdq_status; pdq_last_error() gives a message (per
  *     host thread).  After PDQ_ERR_CUDA / PDQ_ERR_TIMEOUT / PDQ_ERR_INTERNAL the arrays hold
  *     an unspecified permutation of their input pairs.
@@ -72,9 +74,9 @@ typedef struct {
 /* Tuning knobs.  Zero in a field means "library default".  Used by tests to force rare paths
  * (tiny bucket counts and base-case sizes, a zero bad-split budget) on small inputs. */
 typedef struct {
-  int32_t log2_buckets;     /* log2 of buckets per distribution level, 1..10 (default 8) */
+  int32_t log2_buckets;     /* log2 of buckets per distribution level, 1..9 (default 8) */
   int32_t oversample;       /* samples per bucket for splitter selection (default 16) */
-  int32_t base_capacity;    /* largest bucket sorted in shared memory, 16..8192, power of 2 */
+  int32_t base_capacity;    /* largest bucket sorted in shared memory, 256..16384, power of 2 */
   int32_t bad_allowed;      /* >0: start value of the bad-split counter; -1: start at 0 */
   int32_t probe;            /* 0: default (probe on); -1: skip the sorted/reverse probe */
   int32_t reserved[3];

@@ -110,7 +110,7 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
   if (t) {
     if (t->log2_buckets) {
       if (t->log2_buckets < 1 || t->log2_buckets > kLogBMax)
-        return set_error(PDQ_ERR_ARG, "tuning.log2_buckets out of range 1..10");
+        return set_error(PDQ_ERR_ARG, "tuning.log2_buckets out of range 1..9");
       d.logb = t->log2_buckets;
     }
     if (t->oversample) {
@@ -121,7 +121,7 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
     if (t->base_capacity) {
       const int c = t->base_capacity;
       if (c < kBaseCapMin || c > kBaseCapMax || (c & (c - 1)))
-        return set_error(PDQ_ERR_ARG, "tuning.base_capacity must be a power of two in 256..8192");
+        return set_error(PDQ_ERR_ARG, "tuning.base_capacity must be a power of two in 256..16384");
       d.base_cap = c;
     }
     if (t->bad_allowed) d.bad_allowed = t->bad_allowed;
@@ -165,9 +165,9 @@ static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int d
   if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8)
     return set_error(PDQ_ERR_ARG, "value_bytes must be 4 or 8");
   if (n <= 1) return PDQ_OK;
-  if (!keys || ((uintptr_t)keys % kb)) return set_error(PDQ_ERR_ARG, "keys pointer null or misaligned");
-  if (value_bytes && (!vals || ((uintptr_t)vals % value_bytes)))
-    return set_error(PDQ_ERR_ARG, "values pointer null or misaligned");
+  if (!keys || ((uintptr_t)keys % 16)) return set_error(PDQ_ERR_ARG, "keys pointer null or not 16-byte aligned");
+  if (value_bytes && (!vals || ((uintptr_t)vals % 16)))
+    return set_error(PDQ_ERR_ARG, "values pointer null or not 16-byte aligned");
   if (!ws || ((uintptr_t)ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
   SortArgs a;
   a.keys = keys;

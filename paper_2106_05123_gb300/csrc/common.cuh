@@ -9,16 +9,17 @@
 namespace pdq {
 
 // ------------------------------------------------------------------ limits and defaults
-constexpr int kLogBMax = 10;                 // at most 1024 buckets (+ equality buckets) a level
+constexpr int kLogBMax = 9;                  // at most 512 buckets (+ equality buckets) a level
 constexpr int kBMax = 1 << kLogBMax;
 constexpr int kBinsMax = 2 * kBMax;          // bin 2b: keys strictly inside bucket b; 2b+1: == splitter b
 constexpr int kDefaultLogB = 8;
 constexpr int kDefaultOversample = 16;
 constexpr int kMaxSamples = 4096;            // samples sorted in one CTA for splitter selection
-constexpr int kBaseCapMax = 8192;            // largest bucket the shared-memory base sort takes
+constexpr int kBaseCapMax = 16384;           // largest bucket the shared-memory base sort takes
 constexpr int kBaseCapMin = 256;             // smallest base capacity a caller may ask for
 constexpr int kChunkMin = 1 << 14;           // smallest chunk of a task one CTA classifies
 constexpr int kTaskRound = 512;              // tasks split per launch round
+constexpr int kBaseClasses = 5;              // base-sort size classes: 1K, 2K, 4K, 8K, 16K elements
 
 enum Buf : int { kBufKeys = 0, kBufTmp = 1 };
 
@@ -50,7 +51,7 @@ struct Chunk {
 // Device-side counters written by the bookkeeping kernel.
 struct Counters {
   unsigned long long n_next;        // tasks for the next level
-  unsigned long long n_base[4];     // base-sort items per size class
+  unsigned long long n_base[kBaseClasses];  // base-sort items per size class
   unsigned long long n_copy;        // items to copy temp -> keys
   unsigned long long n_fallback;    // items for the merge-path fallback
   unsigned long long equal_buckets;
@@ -58,7 +59,15 @@ struct Counters {
   unsigned long long overflow;      // a list would have exceeded its capacity
   unsigned long long base_elems;    // elements in the base-sort list
   unsigned long long copy_elems;    // elements in the copy list
+  unsigned long long timeout;       // a bounded device-side wait gave up
   unsigned long long probe[8];      // probe results: descents, ascents, min code, max code
+};
+
+// Capacities of the bookkeeping lists (passed by value to the bookkeeping kernel).
+struct ListCaps {
+  int64_t base_off[kBaseClasses];
+  int64_t base_cap[kBaseClasses];
+  int64_t task_cap, copy_cap, fb_cap;
 };
 
 // ------------------------------------------------------------------ key encoding (ordered unsigned)

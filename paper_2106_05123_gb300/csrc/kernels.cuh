@@ -22,8 +22,14 @@
 #pragma once
 
 #include "common.cuh"
+#include "tile_pipe.cuh"
 
 namespace pdq {
+
+template <int N>
+struct IntC {
+  static constexpr int value = N;
+};
 
 // ================================================================== reductions
 template <class T>
@@ -176,6 +182,34 @@ __device__ __forceinline__ int classify(U code, const U* __restrict__ tree,
   return 2 * b + (code == spl[sb] ? 1 : 0);
 }
 
+// Same, with the depth known at compile time (fully unrolled descent).
+template <int LOGB, class U>
+__device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, const U* __restrict__ spl) {
+  int j = 1;
+#pragma unroll
+  for (int l = 0; l < LOGB; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
+  constexpr int B = 1 << LOGB;
+  const int b = j - B;
+  const int sb = b < B - 1 ? b : B - 2;
+  return 2 * b + (code == spl[sb] ? 1 : 0);
+}
+
+// Calls f(std::integral_constant<int, LOGB>) for the runtime depth (uniform per CTA).
+template <class F>
+__device__ __forceinline__ void with_logb(int logb, F&& f) {
+  switch (logb) {
+    case 1: f(IntC<1>()); break;
+    case 2: f(IntC<2>()); break;
+    case 3: f(IntC<3>()); break;
+    case 4: f(IntC<4>()); break;
+    case 5: f(IntC<5>()); break;
+    case 6: f(IntC<6>()); break;
+    case 7: f(IntC<7>()); break;
+    case 8: f(IntC<8>()); break;
+    default: f(IntC<9>()); break;
+  }
+}
+
 // In-order index of Eytzinger node j in a complete tree with B-1 nodes.
 __device__ __forceinline__ int eytz_inorder(int j, int logb) {
   const int d = 31 - __clz(j);
@@ -241,15 +275,23 @@ __device__ __forceinline__ void load_splitters(U* s_tree, U* s_spl, const U* tre
 }
 
 // ================================================================== count
-template <int KT, int THREADS>
+// One CTA per chunk.  Tiles of TILE codes stream into STAGES shared buffers by bulk copy (the
+// ragged <16-byte edges of each tile are classified straight from global memory); every code is
+// classified and counted in a shared histogram, written to counts[chunk][bin] at the end.
+template <int KT, int THREADS, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
              const int32_t* __restrict__ task_logb, const typename Key<KT>::U* __restrict__ keys,
              const typename Key<KT>::U* __restrict__ tmp, const typename Key<KT>::U* __restrict__ tree_g,
-             const typename Key<KT>::U* __restrict__ spl_g, uint32_t* __restrict__ counts) {
+             const typename Key<KT>::U* __restrict__ spl_g, uint32_t* __restrict__ counts, Counters* ctr) {
   using U = typename Key<KT>::U;
+  constexpr int KS = sizeof(U);
+  constexpr int BUF_BYTES = TILE * KS + 16;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[STAGES];
   __shared__ U s_tree[kBMax], s_spl[kBMax];
   __shared__ uint32_t hist[kBinsMax];
+
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
   const int logb = task_logb[c.task];
@@ -257,14 +299,75 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const int nb = 2 * B;
   load_splitters(s_tree, s_spl, tree_g + (size_t)c.task * kBMax, spl_g + (size_t)c.task * kBMax, B);
   for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) mbar_init(&bars[i], 1);
+    fence_proxy_async_smem();
+  }
   __syncthreads();
-  const U* src = (t.buf == kBufKeys ? keys : tmp) + c.begin;
-  if (t.enc) {
-    for (int i = threadIdx.x; i < c.size; i += THREADS)
-      atomicAdd(&hist[classify(src[i], s_tree, s_spl, logb)], 1u);
-  } else {
-    for (int i = threadIdx.x; i < c.size; i += THREADS)
-      atomicAdd(&hist[classify(Key<KT>::enc(src[i]), s_tree, s_spl, logb)], 1u);
+  const U* src = t.buf == kBufKeys ? keys : tmp;
+  const bool enc = t.enc != 0;
+  const int64_t cb = c.begin, ce = c.begin + c.size;
+  const int ntiles = (c.size + TILE - 1) / TILE;
+  auto buf = [&](int stg) { return reinterpret_cast<U*>(smem + (size_t)stg * BUF_BYTES); };
+  auto issue = [&](int tile) {
+    const int64_t s0 = cb + (int64_t)tile * TILE;
+    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
+    const TileGeom<KS> g(s0, e0);
+    const int stg = tile % STAGES;
+    const uint32_t bytes = g.bulk_bytes();
+    mbar_arrive_expect_tx(&bars[stg], bytes);
+    if (bytes) bulk_g2s(buf(stg) + (g.as - g.s_al), src + g.as, bytes, &bars[stg]);
+  };
+  if (threadIdx.x == 0)
+    for (int i = 0; i < STAGES && i < ntiles; ++i) issue(i);
+  uint32_t parity = 0;
+  bool failed = false;
+  with_logb(logb, [&](auto LB) {
+    constexpr int L = decltype(LB)::value;
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const int stg = tile % STAGES;
+      const int64_t s0 = cb + (int64_t)tile * TILE;
+      const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
+      const TileGeom<KS> g(s0, e0);
+      const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
+      parity ^= 1u << stg;
+      if (!__syncthreads_and(ok)) { failed = true; break; }
+      const U* bp = buf(stg);
+      const int k0 = (int)(g.as - g.s_al), k1 = (int)(g.ae - g.s_al);
+      constexpr int ILP = 4;
+      int k = k0 + threadIdx.x;
+      for (; k + (ILP - 1) * THREADS < k1; k += ILP * THREADS) {
+        int bin[ILP];
+#pragma unroll
+        for (int q = 0; q < ILP; ++q) {
+          const U x = bp[k + q * THREADS];
+          bin[q] = classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl);
+        }
+#pragma unroll
+        for (int q = 0; q < ILP; ++q) atomicAdd(&hist[bin[q]], 1u);
+      }
+      for (; k < k1; k += THREADS) {
+        const U x = bp[k];
+        atomicAdd(&hist[classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+      }
+      if ((int)threadIdx.x < g.head + g.tail) {
+        const U x = src[g.edge(s0, threadIdx.x)];
+        atomicAdd(&hist[classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+      }
+      __syncthreads();  // this stage's buffer is consumed
+      if (threadIdx.x == 0 && tile + STAGES < ntiles) {
+        fence_proxy_async_smem();
+        issue(tile + STAGES);
+      }
+    }
+  });
+  if (failed) {
+    // a bulk copy did not complete in time: report, then give in-flight copies a bounded wait
+    if (threadIdx.x == 0) {
+      atomicAdd(&ctr->timeout, 1ull);
+      for (int i = 0; i < STAGES; ++i) mbar_wait_bounded(&bars[i], (parity >> i) & 1u);
+    }
+    return;
   }
   __syncthreads();
   uint32_t* out = counts + (size_t)blockIdx.x * kBinsMax;
@@ -306,21 +409,29 @@ scan_kernel(const int32_t* __restrict__ task_logb, const int32_t* __restrict__ t
 }
 
 // ================================================================== scatter
-// One CTA per chunk; the chunk is processed in tiles of TILE = ITEMS * THREADS elements.
-template <int KT, int VB, int THREADS, int ITEMS>
+// One CTA per chunk, tiles of TILE elements double-buffered in shared memory by bulk copy.
+// Per tile: classify every code, rank it inside its bin with a shared atomic, scan the bin
+// counts, then stage the tile in place grouped by bin (codes and values), and write each bin's
+// run to its next free slots in the destination buffer (coalesced within runs).  Keys of an
+// equality bin written to the key buffer are final and are decoded on the way out.
+template <int KT, int VB, int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS)
 scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
                const int32_t* __restrict__ task_logb, typename Key<KT>::U* __restrict__ keys,
                typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
                typename Val<VB>::T* __restrict__ tmpv, const typename Key<KT>::U* __restrict__ tree_g,
-               const typename Key<KT>::U* __restrict__ spl_g, const uint32_t* __restrict__ offsets) {
+               const typename Key<KT>::U* __restrict__ spl_g, const uint32_t* __restrict__ offsets,
+               Counters* ctr) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
-  constexpr int TILE = THREADS * ITEMS;
+  constexpr int KS = sizeof(U);
+  constexpr int VS = VB ? VB : 4;
+  constexpr int ITEMS = TILE / THREADS;
+  constexpr int KBUF = TILE * KS + 16;
+  constexpr int VBUF = VB ? TILE * VS + 16 : 0;
   extern __shared__ __align__(16) unsigned char smem[];
-  U* stage_k = reinterpret_cast<U*>(smem);
-  V* stage_v = reinterpret_cast<V*>(stage_k + TILE);
-  uint16_t* stage_b = reinterpret_cast<uint16_t*>(VB ? (unsigned char*)(stage_v + TILE) : (unsigned char*)(stage_k + TILE));
+  uint16_t* stage_b = reinterpret_cast<uint16_t*>(smem + 2 * (KBUF + VBUF));
+  __shared__ __align__(8) uint64_t bars[2];
   __shared__ U s_tree[kBMax], s_spl[kBMax];
   __shared__ uint32_t hist[kBinsMax];     // per-tile counts, then tile bin starts
   __shared__ uint32_t cursor[kBinsMax];   // next write offset per bin (task-relative)
@@ -333,34 +444,97 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const int B = 1 << logb;
   const int nb = 2 * B;
   load_splitters(s_tree, s_spl, tree_g + (size_t)c.task * kBMax, spl_g + (size_t)c.task * kBMax, B);
-  for (int b = threadIdx.x; b < nb; b += THREADS) cursor[b] = offsets[(size_t)blockIdx.x * kBinsMax + b];
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    cursor[b] = offsets[(size_t)blockIdx.x * kBinsMax + b];
+    hist[b] = 0;
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
 
   const bool from_keys = t.buf == kBufKeys;
-  const U* srck = (from_keys ? keys : tmpk) + c.begin;
-  const V* srcv = VB ? (from_keys ? vals : tmpv) + c.begin : nullptr;
+  const U* srck = from_keys ? keys : tmpk;
+  const V* srcv = VB ? (from_keys ? vals : tmpv) : nullptr;
   U* dstk = (from_keys ? tmpk : keys) + t.begin;
   V* dstv = VB ? (from_keys ? tmpv : vals) + t.begin : nullptr;
   const bool dst_is_keys = !from_keys;
+  const bool enc = t.enc != 0;
+  const int64_t cb = c.begin, ce = c.begin + c.size;
+  const int ntiles = (c.size + TILE - 1) / TILE;
+  auto kbuf = [&](int stg) { return reinterpret_cast<U*>(smem + (size_t)stg * KBUF); };
+  auto vbuf = [&](int stg) { return reinterpret_cast<V*>(smem + 2 * (size_t)KBUF + (size_t)stg * VBUF); };
 
-  for (int tile0 = 0; tile0 < c.size; tile0 += TILE) {
-    const int cnt = min(TILE, c.size - tile0);
-    for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
-    __syncthreads();
+  // ragged edge elements are fetched at issue time into registers of a few threads
+  // (threads 0..7: keys, 32..39: values) and stored into the buffer before the tile is used
+  U pend_k0 = U(0), pend_k1 = U(0);
+  V pend_v0 = V(0), pend_v1 = V(0);
+  auto issue = [&](int tile) {
+    const int stg = tile & 1;
+    const int64_t s0 = cb + (int64_t)tile * TILE;
+    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
+    const TileGeom<KS> gk(s0, e0);
+    const TileGeom<VS> gv(s0, e0);
+    if (threadIdx.x == 0) {
+      const uint32_t kb = gk.bulk_bytes(), vb = VB ? gv.bulk_bytes() : 0u;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bars[stg], kb + vb);
+      if (kb) bulk_g2s(kbuf(stg) + (gk.as - gk.s_al), srck + gk.as, kb, &bars[stg]);
+      if (VB && vb) bulk_g2s(vbuf(stg) + (gv.as - gv.s_al), srcv + gv.as, vb, &bars[stg]);
+    }
+    const int tid = threadIdx.x;
+    if (tid < 8 && tid < gk.head + gk.tail) {
+      const U x = srck[gk.edge(s0, tid)];
+      if (stg) pend_k1 = x; else pend_k0 = x;
+    }
+    if (VB && tid >= 32 && tid < 40 && tid - 32 < gv.head + gv.tail) {
+      const V x = srcv[gv.edge(s0, tid - 32)];
+      if (stg) pend_v1 = x; else pend_v0 = x;
+    }
+  };
+  issue(0);
+  if (ntiles > 1) issue(1);
+
+  uint32_t parity = 0;
+  bool failed = false;
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int stg = tile & 1;
+    const int64_t s0 = cb + (int64_t)tile * TILE;
+    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
+    const int cnt = (int)(e0 - s0);
+    const TileGeom<KS> gk(s0, e0);
+    const TileGeom<VS> gv(s0, e0);
+    U* bk = kbuf(stg);
+    V* bv = VB ? vbuf(stg) : nullptr;
+    {
+      const int tid = threadIdx.x;
+      if (tid < 8 && tid < gk.head + gk.tail) bk[gk.edge(s0, tid) - gk.s_al] = stg ? pend_k1 : pend_k0;
+      if (VB && tid >= 32 && tid < 40 && tid - 32 < gv.head + gv.tail)
+        bv[gv.edge(s0, tid - 32) - gv.s_al] = stg ? pend_v1 : pend_v0;
+    }
+    const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
+    parity ^= 1u << stg;
+    if (!__syncthreads_and(ok)) { failed = true; break; }
+
     U code[ITEMS];
     V val[ITEMS];
-    int bin[ITEMS];
-    uint32_t rank[ITEMS];
+    uint32_t packed[ITEMS];  // bin << 16 | rank inside the bin
+    with_logb(logb, [&](auto LB) {
+      constexpr int L = decltype(LB)::value;
 #pragma unroll
-    for (int e = 0; e < ITEMS; ++e) {
-      const int i = e * THREADS + threadIdx.x;
-      if (i < cnt) {
-        const U x = srck[tile0 + i];
-        code[e] = t.enc ? x : Key<KT>::enc(x);
-        if (VB) val[e] = srcv[tile0 + i];
-        bin[e] = classify(code[e], s_tree, s_spl, logb);
-        rank[e] = atomicAdd(&hist[bin[e]], 1u);
+      for (int e = 0; e < ITEMS; ++e) {
+        const int i = e * THREADS + threadIdx.x;
+        if (i < cnt) {
+          const U x = bk[gk.off + i];
+          code[e] = enc ? x : Key<KT>::enc(x);
+          if (VB) val[e] = bv[gv.off + i];
+          const int bin = classify_t<L>(code[e], s_tree, s_spl);
+          packed[e] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
+        }
       }
-    }
+    });
     __syncthreads();
     block_exclusive_scan<THREADS>(hist, hist, nb, wtmp);  // hist := tile start of each bin
     for (int b = threadIdx.x; b < nb; b += THREADS) {
@@ -368,26 +542,34 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
       gbase[b] = cursor[b] - hist[b];
       cursor[b] += next - hist[b];
     }
+    // stage in place: every thread has read its codes from the buffer (scan barriers above)
 #pragma unroll
     for (int e = 0; e < ITEMS; ++e) {
       const int i = e * THREADS + threadIdx.x;
       if (i < cnt) {
-        const uint32_t p = hist[bin[e]] + rank[e];
-        stage_k[p] = code[e];
-        if (VB) stage_v[p] = val[e];
-        stage_b[p] = (uint16_t)bin[e];
+        const uint32_t bin = packed[e] >> 16;
+        const uint32_t p = hist[bin] + (packed[e] & 0xFFFFu);
+        bk[p] = code[e];
+        if (VB) bv[p] = val[e];
+        stage_b[p] = (uint16_t)bin;
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += THREADS) {
       const int b = stage_b[i];
       const uint32_t o = gbase[b] + (uint32_t)i;
-      U k = stage_k[i];
+      U k = bk[i];
       if (dst_is_keys && (b & 1)) k = Key<KT>::dec(k);  // equality bin: final, decode now
       dstk[o] = k;
-      if (VB) dstv[o] = stage_v[i];
+      if (VB) dstv[o] = bv[i];
     }
-    __syncthreads();
+    __syncthreads();  // buffer, stage_b and hist are free again
+    for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+    if (tile + 2 < ntiles) issue(tile + 2);
+  }
+  if (failed && threadIdx.x == 0) {
+    atomicAdd(&ctr->timeout, 1ull);
+    for (int i = 0; i < 2; ++i) mbar_wait_bounded(&bars[i], (parity >> i) & 1u);
   }
 }
 
@@ -396,7 +578,7 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
                                 const uint2* __restrict__ children, int base_cap, Counters* ctr,
                                 Task* __restrict__ next, Item* __restrict__ base_items,
                                 Item* __restrict__ copy_items, Item* __restrict__ fb_items,
-                                int64_t task_cap, int64_t item_cap) {
+                                ListCaps caps) {
   const int task = blockIdx.y;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int nb = 2 << task_logb[task];
@@ -410,21 +592,22 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   it.size = ch.y;
   it.buf = (uint16_t)dst;
   it.enc = 1;
-  auto push = [&](Item* list, unsigned long long* counter) {
+  auto push = [&](Item* list, unsigned long long* counter, int64_t cap) {
     const unsigned long long k = atomicAdd(counter, 1ull);
-    if ((int64_t)k < item_cap) list[k] = it;
+    if ((int64_t)k < cap) list[k] = it;
     else atomicAdd(&ctr->overflow, 1ull);
   };
   if (b & 1) {  // equality bucket: every key equals the splitter, final (Sec. 3)
     atomicAdd(&ctr->equal_buckets, 1ull);
     if (dst == kBufTmp) {
-      push(copy_items, &ctr->n_copy);
+      push(copy_items, &ctr->n_copy, caps.copy_cap);
       atomicAdd(&ctr->copy_elems, (unsigned long long)ch.y);
     }
     return;
   }
   if ((int64_t)ch.y <= base_cap) {
-    push(base_items, &ctr->n_base[0]);
+    const int cls = ch.y <= 1024u ? 0 : (ch.y <= 2048u ? 1 : (ch.y <= 4096u ? 2 : (ch.y <= 8192u ? 3 : 4)));
+    push(base_items + caps.base_off[cls], &ctr->n_base[cls], caps.base_cap[cls]);
     atomicAdd(&ctr->base_elems, (unsigned long long)ch.y);
     return;
   }
@@ -433,7 +616,7 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   if (bad) atomicAdd(&ctr->bad_splits, 1ull);
   const int left = t.bad_left - (bad ? 1 : 0);
   if (left <= 0) {
-    push(fb_items, &ctr->n_fallback);
+    push(fb_items, &ctr->n_fallback, caps.fb_cap);
     return;
   }
   Task nt;
@@ -444,68 +627,177 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   nt.bad_left = left;
   nt.attempt = t.attempt + 1;
   const unsigned long long k = atomicAdd(&ctr->n_next, 1ull);
-  if ((int64_t)k < task_cap) next[k] = nt;
+  if ((int64_t)k < caps.task_cap) next[k] = nt;
   else atomicAdd(&ctr->overflow, 1ull);
 }
 
 // ================================================================== base sort (Sec. 5.1)
-// One CTA per item of at most CAP elements: load into shared memory (encoding raw keys), pad to
-// a power of two with the largest code, bitonic-sort, write to the output buffer (decoded when
-// `decode`).  With a payload, the sort key is (code, index) so padding sorts after real keys and
-// values are gathered through the index.
-template <int KT, int VB, int THREADS>
+// One CTA per bucket of at most CAP = THREADS * ITEMS elements, sorted in shared memory by a
+// register-blocked merge sort: every thread sorts ITEMS consecutive codes in registers with a
+// compile-time bitonic network, then log2(active threads) merge-path rounds double the sorted
+// runs.  Shared-memory indices are padded (one word per 32) so the blocked per-thread accesses
+// are free of bank conflicts.  With a payload the sort key is (code, original position), which
+// also orders the padding (largest code, positions >= m) after real keys; values are gathered
+// through the positions at the end.  Without a payload, padding and real largest-code keys are
+// identical bit patterns, so the first m outputs are correct whatever their order.
+// Padded capacity of the shared arrays: CAP plus one pad element per 32 (4-byte codes) or per
+// 16 (8-byte codes), rounded up to a multiple of 4 so that each array that follows (positions,
+// values) starts 16-byte aligned.
+template <int KS>
+__host__ __device__ constexpr int base_sort_pcap(int cap) {
+  return (cap + cap / (KS == 4 ? 32 : 16) + 1 + 3) / 4 * 4;
+}
+
+template <class U>
+__device__ __forceinline__ int pad_idx(int x) {
+  return sizeof(U) == 4 ? x + (x >> 5) : x + (x >> 4);
+}
+
+// (a, ia) precedes (b, ib): by code, then by position when WITH_IDX
+template <bool WITH_IDX, class U>
+__device__ __forceinline__ bool precedes(U a, uint32_t ia, U b, uint32_t ib) {
+  if (WITH_IDX) return a < b || (a == b && ia < ib);
+  return a < b;
+}
+
+template <bool WITH_IDX, int N, class U>
+__device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
+#pragma unroll
+  for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & kk) == 0;
+          const bool gt = precedes<WITH_IDX>(k[l], x[l], k[i], x[i]);  // (k[i],x[i]) > (k[l],x[l])
+          if (gt == up) {
+            const U t = k[i]; k[i] = k[l]; k[l] = t;
+            if (WITH_IDX) { const uint32_t y = x[i]; x[i] = x[l]; x[l] = y; }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int KT, int VB, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS)
-base_sort_kernel(const Item* __restrict__ items, int cap, typename Key<KT>::U* __restrict__ keys,
+base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict__ keys,
                  typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
                  typename Val<VB>::T* __restrict__ tmpv, int out_buf, int decode) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
+  constexpr bool W = VB > 0;
+  constexpr int CAP = THREADS * ITEMS;
+  constexpr int PCAP = base_sort_pcap<sizeof(U)>(CAP);
+  static_assert(PCAP % 4 == 0, "padded arrays must keep 16-byte alignment of the next array");
   extern __shared__ __align__(16) unsigned char smem[];
   U* sk = reinterpret_cast<U*>(smem);
-  V* sv = reinterpret_cast<V*>(sk + cap);
-  uint32_t* si = reinterpret_cast<uint32_t*>(VB ? (unsigned char*)(sv + cap) : (unsigned char*)(sk + cap));
+  uint32_t* si = reinterpret_cast<uint32_t*>(sk + PCAP);
+  V* sv = reinterpret_cast<V*>(si + (W ? PCAP : 0));
+
   const Item it = items[blockIdx.x];
   const int m = (int)it.size;
-  const int P = (int)next_pow2_u32(m < 2 ? 2 : (uint32_t)m);
+  const int tid = threadIdx.x;
+  // active threads: a power of two covering m
+  int na = 1;
+  while (na * ITEMS < m) na <<= 1;
+  const int P = na * ITEMS;
   const U* srck = (it.buf == kBufKeys ? keys : tmpk) + it.begin;
-  const V* srcv = VB ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
-  for (int i = threadIdx.x; i < P; i += THREADS) {
+  const V* srcv = W ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
+  for (int i = tid; i < P; i += THREADS) {
+    U c = ~U(0);
     if (i < m) {
       const U x = srck[i];
-      sk[i] = it.enc ? x : Key<KT>::enc(x);
-      if (VB) sv[i] = srcv[i];
-    } else {
-      sk[i] = ~U(0);
+      c = it.enc ? x : Key<KT>::enc(x);
+      if (W) sv[i] = srcv[i];
     }
-    if (VB) si[i] = i;
+    sk[pad_idx<U>(i)] = c;
+    if (W) si[pad_idx<U>(i)] = (uint32_t)i;
   }
   __syncthreads();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int q = threadIdx.x; q < P / 2; q += THREADS) {
-        const int i = (q / j) * 2 * j + (q % j);
-        const int l = i + j;
-        const bool up = (i & k) == 0;
-        const U a = sk[i], b = sk[l];
-        bool gt;
-        if (VB) gt = a > b || (a == b && si[i] > si[l]);
-        else gt = a > b;
-        if (gt == up) {
-          sk[i] = b;
-          sk[l] = a;
-          if (VB) { const uint32_t x = si[i]; si[i] = si[l]; si[l] = x; }
+  U k[ITEMS];
+  uint32_t x[ITEMS];
+  const bool active = tid < na;
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < ITEMS; ++e) {
+      const int p = pad_idx<U>(tid * ITEMS + e);
+      k[e] = sk[p];
+      x[e] = W ? si[p] : 0u;
+    }
+    register_sort<W>(k, x);
+  }
+  for (int R = ITEMS; R < P; R <<= 1) {
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        const int p = pad_idx<U>(tid * ITEMS + e);
+        sk[p] = k[e];
+        if (W) si[p] = x[e];
+      }
+    }
+    __syncthreads();
+    if (active) {
+      const int pos = tid * ITEMS;
+      const int g = pos & ~(2 * R - 1);  // first element of the pair of runs
+      const int d = pos - g;             // this thread's diagonal inside the pair
+      const int a0 = g, b0 = g + R;
+      int lo = d > R ? d - R : 0;
+      int hi = d < R ? d : R;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const int pa = pad_idx<U>(a0 + mid), pb = pad_idx<U>(b0 + d - 1 - mid);
+        if (!precedes<W>(sk[pb], W ? si[pb] : 0u, sk[pa], W ? si[pa] : 0u)) lo = mid + 1;
+        else hi = mid;
+      }
+      int ai = lo, bi = d - lo;
+      U ka = k[0], kb = k[0];
+      uint32_t xa = 0, xb = 0;
+      if (ai < R) { const int p = pad_idx<U>(a0 + ai); ka = sk[p]; if (W) xa = si[p]; }
+      if (bi < R) { const int p = pad_idx<U>(b0 + bi); kb = sk[p]; if (W) xb = si[p]; }
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        const bool a_ok = ai < R, b_ok = bi < R;
+        const bool take_a = a_ok && (!b_ok || !precedes<W>(kb, xb, ka, xa));
+        k[e] = take_a ? ka : kb;
+        x[e] = take_a ? xa : xb;
+        if (take_a) {
+          ++ai;
+          if (ai < R) { const int p = pad_idx<U>(a0 + ai); ka = sk[p]; if (W) xa = si[p]; }
+        } else {
+          ++bi;
+          if (bi < R) { const int p = pad_idx<U>(b0 + bi); kb = sk[p]; if (W) xb = si[p]; }
         }
       }
-      __syncthreads();
     }
   }
-  U* dstk = (out_buf == kBufKeys ? keys : tmpk) + it.begin;
-  V* dstv = VB ? (out_buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
-  for (int i = threadIdx.x; i < m; i += THREADS) {
-    const U k = sk[i];
-    dstk[i] = decode ? Key<KT>::dec(k) : k;
-    if (VB) dstv[i] = sv[si[i]];
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int e = 0; e < ITEMS; ++e) {
+      const int p = pad_idx<U>(tid * ITEMS + e);
+      sk[p] = k[e];
+      if (W) si[p] = x[e];
+    }
   }
+  __syncthreads();
+  U* dstk = (out_buf == kBufKeys ? keys : tmpk) + it.begin;
+  V* dstv = W ? (out_buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
+  for (int i = tid; i < m; i += THREADS) {
+    const int p = pad_idx<U>(i);
+    const U c = sk[p];
+    dstk[i] = decode ? Key<KT>::dec(c) : c;
+    if (W) dstv[i] = sv[si[p]];
+  }
+}
+
+template <int KS, int VB, int THREADS, int ITEMS>
+constexpr size_t base_sort_smem() {
+  return (size_t)base_sort_pcap<KS>(THREADS * ITEMS) * (KS + (VB ? 4 : 0)) + (size_t)THREADS * ITEMS * VB;
 }
 
 // ================================================================== copy temp -> keys (decode)

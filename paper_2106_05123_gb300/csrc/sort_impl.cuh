@@ -27,6 +27,15 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
   L.round_cap = std::min<int64_t>(kTaskRound, L.task_cap);
   L.chunk_cap = n / chunk_min_for(n) + 1 + L.round_cap;
   L.item_cap = std::min<int64_t>(L.round_cap * kBMax, n + 1);
+  L.fb_cap = n / (cmin + 1) + 2;
+  // base-sort lists: class 0 (<= 1024 elements) may hold item_cap entries; an item of class
+  // c >= 1 has more than 512 << c elements, so that list needs at most n / (512 << c) + 1.
+  int64_t base_total = 0;
+  for (int c = 0; c < kBaseClasses; ++c) {
+    L.base_cap[c] = c == 0 ? L.item_cap : std::min<int64_t>(L.item_cap, n / ((int64_t)512 << c) + 1);
+    L.base_off[c] = base_total;
+    base_total += L.base_cap[c];
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -44,9 +53,9 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
   L.tree = take((size_t)L.round_cap * kBMax * ks);
   L.spl = take((size_t)L.round_cap * kBMax * ks);
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
-  L.base_items = take((size_t)L.item_cap * sizeof(Item));
+  L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
-  L.fb_items = take((size_t)L.item_cap * sizeof(Item));
+  L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
   L.total = off;
   return L;
 }
@@ -54,16 +63,29 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
 // ------------------------------------------------------------------ tile shapes
 template <int KS, int VB>
 struct Shape {
+  // scatter: 512 threads, a 32 KiB tile of codes+values (power-of-two element count), double
+  // buffered, staged in place; plus 2 bytes of bin id per element
   static constexpr int kScatterThreads = 512;
-  static constexpr int kBytes = KS + VB;
-  static constexpr int kItems = kBytes <= 4 ? 16 : (kBytes <= 8 ? 8 : 4);
-  static constexpr int kTile = kScatterThreads * kItems;
-  static constexpr size_t kScatterSmem = (size_t)kTile * (KS + VB + 2);
+  static constexpr int kScatterTile = (KS + VB) <= 4 ? 8192 : ((KS + VB) <= 8 ? 4096 : 2048);
+  static constexpr size_t kScatterSmem =
+      2 * ((size_t)kScatterTile * KS + 16 + (VB ? (size_t)kScatterTile * VB + 16 : 0)) + (size_t)kScatterTile * 2;
+  // count: 512 threads, four 16 KiB tiles in flight
   static constexpr int kCountThreads = 512;
+  static constexpr int kCountTile = 16384 / KS;
+  static constexpr int kCountStages = 4;
+  static constexpr size_t kCountSmem = (size_t)kCountStages * (kCountTile * KS + 16);
   static constexpr int kSampleThreads = 512;
-  static constexpr int kBaseThreads = 256;
-  static constexpr size_t base_smem(int cap) { return (size_t)cap * (KS + VB + (VB ? 4 : 0)); }
+  // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
+  // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits)
+  static constexpr int kBaseItems = KS == 4 ? 16 : 8;
+  static constexpr int base_threads(int cls) { return (1024 << cls) / kBaseItems; }
+  static constexpr int kMaxClass = (KS == 4 && VB <= 4) ? 4 : 3;
+  static constexpr int kMaxCap = 1024 << kMaxClass;
 };
+
+inline int base_class_of(int64_t m) {
+  return m <= 1024 ? 0 : (m <= 2048 ? 1 : (m <= 4096 ? 2 : (m <= 8192 ? 3 : 4)));
+}
 
 #define PDQ_CUDA(expr)                                                                  \
   do {                                                                                  \
@@ -88,6 +110,7 @@ class PlainSorter {
 
  public:
   PlainSorter(const SortArgs& a) : a_(a) {
+    cap_ = std::min(a.tune.base_cap, S::kMaxCap);
     L_ = make_layout(a.n, KS, VB);
     char* ws = static_cast<char*>(a.ws);
     keys_ = static_cast<U*>(a.keys);
@@ -115,11 +138,13 @@ class PlainSorter {
     if (rc) return rc;
     const int64_t n = a_.n;
     if (n <= 1) return PDQ_OK;
-    const int cap = a_.tune.base_cap;
+    const int cap = cap_;
     if (n <= cap) {
       Item it{0, (uint32_t)n, kBufKeys, 0};
-      PDQ_CUDA(cudaMemcpyAsync(base_items_, &it, sizeof(it), cudaMemcpyHostToDevice, st_));
-      return base_sort(1, kBufKeys, 1, n);
+      const int cls = base_class_of(n);
+      PDQ_CUDA(cudaMemcpyAsync(base_items_ + L_.base_off[cls], &it, sizeof(it),
+                               cudaMemcpyHostToDevice, st_));
+      return base_sort(cls, 1, kBufKeys, 1, n);
     }
     if (a_.tune.probe) {
       bool done = false;
@@ -153,6 +178,7 @@ class PlainSorter {
  private:
   SortArgs a_;
   Layout L_;
+  int cap_;  // base capacity for this key/value width
   U *keys_, *tmpk_, *tree_, *spl_;
   V *vals_, *tmpv_;
   Counters* ctr_;
@@ -164,14 +190,30 @@ class PlainSorter {
   Item *base_items_, *copy_items_, *fb_items_;
   cudaStream_t st_;
 
+  template <int CLS>
+  int configure_base() {
+    constexpr int T = S::base_threads(CLS);
+    PDQ_CUDA(cudaFuncSetAttribute(base_sort_kernel<KT, VB, T, S::kBaseItems>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)base_sort_smem<KS, VB, T, S::kBaseItems>()));
+    return PDQ_OK;
+  }
+
   int configure() {
     static bool done = false;  // per template instantiation
     if (done) return PDQ_OK;
-    PDQ_CUDA(cudaFuncSetAttribute(scatter_kernel<KT, VB, S::kScatterThreads, S::kItems>,
+    PDQ_CUDA(cudaFuncSetAttribute(scatter_kernel<KT, VB, S::kScatterThreads, S::kScatterTile>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kScatterSmem));
-    PDQ_CUDA(cudaFuncSetAttribute(base_sort_kernel<KT, VB, S::kBaseThreads>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)S::base_smem(kBaseCapMax)));
+    PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, S::kCountThreads, S::kCountTile, S::kCountStages>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kCountSmem));
+    int rc = configure_base<0>();
+    if (!rc) rc = configure_base<1>();
+    if (!rc) rc = configure_base<2>();
+    if (!rc) rc = configure_base<3>();
+    if constexpr (S::kMaxClass >= 4) {
+      if (!rc) rc = configure_base<4>();
+    }
+    if (rc) return rc;
     done = true;
     return PDQ_OK;
   }
@@ -227,9 +269,11 @@ class PlainSorter {
     return PDQ_OK;
   }
 
+  // Buckets per level: enough that the expected bucket is a quarter of the base capacity (so
+  // that, with sampling noise, almost every bucket fits the base sort after this level).
   int choose_logb(int64_t size) const {
-    const int64_t half = std::max<int64_t>(1, a_.tune.base_cap / 2);
-    const int64_t want = (size + half - 1) / half;
+    const int64_t quarter = std::max<int64_t>(1, cap_ / 4);
+    const int64_t want = (size + quarter - 1) / quarter;
     int lb = 1;
     while ((int64_t(1) << lb) < want && lb < a_.tune.logb) ++lb;
     return lb;
@@ -275,8 +319,9 @@ class PlainSorter {
     PDQ_LAUNCHED("sample");
     {
       LaunchScope ls("count", st_, (double)total * KS);
-      count_kernel<KT, S::kCountThreads><<<nchunks, S::kCountThreads, 0, st_>>>(
-          chunks_, tasks_, d_logb, keys_, tmpk_, tree_, spl_, counts_);
+      count_kernel<KT, S::kCountThreads, S::kCountTile, S::kCountStages>
+          <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, d_logb, keys_, tmpk_, tree_,
+                                                              spl_, counts_, ctr_);
     }
     PDQ_LAUNCHED("count");
     {
@@ -286,27 +331,36 @@ class PlainSorter {
     PDQ_LAUNCHED("scan");
     {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
-      scatter_kernel<KT, VB, S::kScatterThreads, S::kItems>
+      scatter_kernel<KT, VB, S::kScatterThreads, S::kScatterTile>
           <<<nchunks, S::kScatterThreads, S::kScatterSmem, st_>>>(
-              chunks_, tasks_, d_logb, keys_, vals_, tmpk_, tmpv_, tree_, spl_, counts_);
+              chunks_, tasks_, d_logb, keys_, vals_, tmpk_, tmpv_, tree_, spl_, counts_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
     {
       LaunchScope ls("bookkeep", st_, 0.0);
       dim3 grid((unsigned)((2 << max_logb) + 255) / 256, (unsigned)nt);
-      bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_logb, children_, a_.tune.base_cap, ctr_, next_,
-                                               base_items_, copy_items_, fb_items_, L_.task_cap,
-                                               L_.item_cap);
+      ListCaps caps;
+      for (int c = 0; c < kBaseClasses; ++c) {
+        caps.base_off[c] = L_.base_off[c];
+        caps.base_cap[c] = L_.base_cap[c];
+      }
+      caps.task_cap = L_.task_cap;
+      caps.copy_cap = L_.item_cap;
+      caps.fb_cap = L_.fb_cap;
+      bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_logb, children_, cap_, ctr_, next_,
+                                               base_items_, copy_items_, fb_items_, caps);
     }
     PDQ_LAUNCHED("bookkeep");
     Counters h;
     PDQ_CUDA(cudaMemcpyAsync(&h, ctr_, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
     PDQ_CUDA(cudaStreamSynchronize(st_));
+    if (h.timeout) return set_error(PDQ_ERR_TIMEOUT, "a tile copy did not complete within its bounded wait");
     if (h.overflow) return set_error(PDQ_ERR_INTERNAL, "bookkeeping list capacity exceeded");
     stats_.equal_buckets += (int64_t)h.equal_buckets;
     stats_.bad_splits += (int64_t)h.bad_splits;
-    if (h.n_base[0]) {
-      int rc = base_sort((int64_t)h.n_base[0], kBufKeys, 1, (int64_t)h.base_elems);
+    for (int cls = 0; cls < kBaseClasses; ++cls) {
+      if (!h.n_base[cls]) continue;
+      int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, cls == 0 ? (int64_t)h.base_elems : 0);
       if (rc) return rc;
     }
     if (h.n_copy) {
@@ -334,41 +388,59 @@ class PlainSorter {
     return PDQ_OK;
   }
 
-  // Base sort of `count` items (holding `elems` elements) already in base_items_.
-  int base_sort(int64_t count, int out_buf, int decode, int64_t elems) {
-    const int cap = a_.tune.base_cap;
-    stats_.base_buckets += count;
+  // Base sort of `count` items of size class `cls` (holding `elems` elements for the byte
+  // accounting) already in that class's list.
+  template <int CLS>
+  int base_sort_cls(int64_t count, int out_buf, int decode, int64_t elems) {
+    constexpr int T = S::base_threads(CLS);
+    constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
+    const Item* list = base_items_ + L_.base_off[CLS];
     for (int64_t done = 0; done < count;) {
       const int64_t g = std::min<int64_t>(count - done, 1 << 30);
       LaunchScope ls("base_sort", st_, done == 0 ? 2.0 * (double)elems * (KS + VB) : 0.0);
-      base_sort_kernel<KT, VB, S::kBaseThreads><<<(unsigned)g, S::kBaseThreads, S::base_smem(cap), st_>>>(
-          base_items_ + done, cap, keys_, vals_, tmpk_, tmpv_, out_buf, decode);
+      base_sort_kernel<KT, VB, T, S::kBaseItems><<<(unsigned)g, T, smem, st_>>>(
+          list + done, keys_, vals_, tmpk_, tmpv_, out_buf, decode);
       done += g;
     }
     PDQ_LAUNCHED("base_sort");
     return PDQ_OK;
   }
 
+  int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems) {
+    stats_.base_buckets += count;
+    switch (cls) {
+      case 0: return base_sort_cls<0>(count, out_buf, decode, elems);
+      case 1: return base_sort_cls<1>(count, out_buf, decode, elems);
+      case 2: return base_sort_cls<2>(count, out_buf, decode, elems);
+      case 3: return base_sort_cls<3>(count, out_buf, decode, elems);
+      default:
+        if constexpr (S::kMaxClass >= 4) return base_sort_cls<4>(count, out_buf, decode, elems);
+        return set_error(PDQ_ERR_INTERNAL, "base class out of range");
+    }
+  }
+
   // O(n log n) fallback for one bucket (Sec. 4.1): shared-memory sorts of runs of base_cap
   // elements, then merge-path passes, ping-ponging between the key and temp buffers so that
   // the last pass lands decoded in the key buffer.
   int fallback(const Item& it) {
-    const int64_t run = a_.tune.base_cap;
+    const int64_t run = cap_;
     int passes = 0;
     while ((run << passes) < (int64_t)it.size) ++passes;
     const int x = (passes % 2 == 0) ? kBufKeys : kBufTmp;
     const int64_t ntiles = ((int64_t)it.size + run - 1) / run;
     std::vector<Item> tiles;
     for (int64_t t0 = 0; t0 < ntiles;) {
-      const int64_t t1 = std::min<int64_t>(ntiles, t0 + L_.item_cap);
+      const int64_t t1 = std::min<int64_t>(ntiles, t0 + L_.base_cap[base_class_of(run)]);
       tiles.clear();
       for (int64_t t = t0; t < t1; ++t) {
         const int64_t b = t * run;
         tiles.push_back(Item{it.begin + b, (uint32_t)std::min<int64_t>(run, (int64_t)it.size - b), it.buf, it.enc});
       }
-      PDQ_CUDA(cudaMemcpyAsync(base_items_, tiles.data(), sizeof(Item) * tiles.size(), cudaMemcpyHostToDevice, st_));
+      const int cls = base_class_of(run);
+      PDQ_CUDA(cudaMemcpyAsync(base_items_ + L_.base_off[cls], tiles.data(), sizeof(Item) * tiles.size(),
+                               cudaMemcpyHostToDevice, st_));
       const int64_t tile_elems = std::min<int64_t>((int64_t)it.size - t0 * run, (t1 - t0) * run);
-      int rc = base_sort((int64_t)tiles.size(), x, passes == 0 ? 1 : 0, tile_elems);
+      int rc = base_sort(cls, (int64_t)tiles.size(), x, passes == 0 ? 1 : 0, tile_elems);
       if (rc) return rc;
       stats_.base_buckets -= (int64_t)tiles.size();  // tiles are not buckets
       PDQ_CUDA(cudaStreamSynchronize(st_));  // tiles buffer is reused by the next batch

@@ -1,0 +1,95 @@
+// Tile staging for the streaming kernels: 1-D bulk copies (TMA engine, cp.async.bulk) from
+// global into shared memory, completion tracked by mbarriers.
+//
+// A tile [s, e) of elements of size ES lives in a shared buffer whose element k holds global
+// element s_al + k, s_al = s rounded down to a 16-byte boundary.  The 16-byte-aligned interior
+// [as, ae) is one bulk copy; the ragged head [s, as) and tail [ae, e) (fewer than 16/ES elements
+// each) are fetched with plain loads by a few threads and stored into the buffer before the
+// consuming barrier.  Every wait is bounded: after kWaitNs of polling the waiter reports failure.
+#pragma once
+
+#include "common.cuh"
+
+namespace pdq {
+
+constexpr uint64_t kWaitNs = 1000000000ull;  // a wait on an mbarrier gives up after one second
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// Makes mbarrier initialisation and earlier generic-proxy shared-memory accesses visible to
+// the async proxy (the bulk-copy engine).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) into shared memory,
+// signalling `bar` with the byte count on completion.
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst_smem)),
+      "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase with the given parity; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+
+// Geometry of one tile of elements of ES bytes inside its 16-byte-aligned shared buffer.
+template <int ES>
+struct TileGeom {
+  static constexpr int kAlign = 16 / ES;  // elements per 16 bytes
+  int64_t s_al;   // global index held by buffer element 0
+  int64_t as, ae; // bulk-copied interior [as, ae)
+  int head, tail; // ragged elements [s, as) and [ae, e)
+  int off;        // buffer index of the tile's first element (s - s_al)
+
+  __device__ __forceinline__ TileGeom(int64_t s, int64_t e) {
+    s_al = s - (s % kAlign);
+    int64_t a = s_al == s ? s : s_al + kAlign;
+    as = a < e ? a : e;
+    int64_t b = e - (e % kAlign);
+    ae = b > as ? b : as;
+    head = (int)(as - s);
+    tail = (int)(e - ae);
+    off = (int)(s - s_al);
+  }
+  __device__ __forceinline__ uint32_t bulk_bytes() const { return (uint32_t)((ae - as) * ES); }
+  // global index of ragged element j (j < head + tail)
+  __device__ __forceinline__ int64_t edge(int64_t s, int j) const { return j < head ? s + j : ae + (j - head); }
+};
+
+}  // namespace pdq

@@ -64,6 +64,6 @@ def test_argument_errors_need_no_device(L):
     assert L.pdq_sort_keys(ctypes.c_void_p(4096), 10, 0, ctypes.c_void_p(4100), 1 << 20, None, None,
                            ctypes.byref(st)) == -3
     # bad tuning values
-    bad = pdq.Tuning(log2_buckets=11)
+    bad = pdq.Tuning(log2_buckets=10)
     assert L.pdq_sort_keys(ctypes.c_void_p(4096), 10, 0, ctypes.c_void_p(4096), 1 << 20, None,
                            ctypes.byref(bad), ctypes.byref(st)) in (-1, -3)

@@ -53,7 +53,7 @@ TUNINGS = [
     dict(log2_buckets=1, base_capacity=256),                # two-way splits: many levels
     dict(log2_buckets=2, oversample=1, base_capacity=256),  # poor samples: bad splits likely
     dict(log2_buckets=3, base_capacity=512),
-    dict(log2_buckets=10, base_capacity=256),               # widest level
+    dict(log2_buckets=9, base_capacity=256),                # widest level
     dict(bad_allowed=-1, base_capacity=256),                # counter starts at 0: fallback only
     dict(bad_allowed=1, log2_buckets=1, oversample=1, base_capacity=256),  # early fallback
     dict(probe=-1),
