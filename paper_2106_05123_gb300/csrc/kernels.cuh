@@ -194,6 +194,44 @@ __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, co
   return 2 * b + (code == spl[sb] ? 1 : 0);
 }
 
+// Exact rank prefilter over the splitter range [lo, hi] = [spl[0], spl[B-2]]: entry k of `tab`
+// covers the codes lo + [k << shift, (k + 1) << shift) and stores (b_lo | b_hi << 16) with
+// b_lo = #splitters < first code and b_hi = #splitters <= last code of the slice, so every
+// code of the slice has rank (#splitters < code) in [b_lo, b_hi].  Codes outside [lo, hi] are
+// clamped into the first or last slice, whose bounds still hold for them.
+constexpr int kPrefBits = 11;
+constexpr int kPrefEntries = 1 << kPrefBits;
+
+template <class U>
+struct Pref {
+  U lo, hi;
+  int shift;
+  int nent;
+};
+
+// Bin of a code: a prefilter slice with at most one candidate splitter settles the rank with
+// one predicated comparison (branch-free); a wider slice falls back to the Eytzinger descent.
+template <int LOGB, class U>
+__device__ __forceinline__ int classify_fast(U code, const U* __restrict__ tree, const U* __restrict__ spl,
+                                             const uint32_t* __restrict__ tab, const Pref<U>& pf) {
+  constexpr int B = 1 << LOGB;
+  const U y = code < pf.lo ? pf.lo : (code > pf.hi ? pf.hi : code);
+  const uint32_t e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
+  const int blo = (int)(e & 0xFFFFu), bhi = (int)(e >> 16);
+  int b;
+  if (bhi - blo <= 1) {
+    const int k = blo < B - 2 ? blo : B - 2;  // == blo whenever blo < bhi
+    b = blo + ((blo < bhi && spl[k] < code) ? 1 : 0);
+  } else {
+    int j = 1;
+#pragma unroll
+    for (int l = 0; l < LOGB; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
+    b = j - B;
+  }
+  const int sb = b < B - 1 ? b : B - 2;
+  return 2 * b + (code == spl[sb] ? 1 : 0);
+}
+
 // Calls f(std::integral_constant<int, LOGB>) for the runtime depth (uniform per CTA).
 template <class F>
 __device__ __forceinline__ void with_logb(int logb, F&& f) {
@@ -226,7 +264,8 @@ template <int KT, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_logb, int oversample,
               const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
-              typename Key<KT>::U* __restrict__ tree_out, typename Key<KT>::U* __restrict__ spl_out) {
+              typename Key<KT>::U* __restrict__ tree_out, typename Key<KT>::U* __restrict__ spl_out,
+              Pref<typename Key<KT>::U>* __restrict__ pref_out, uint32_t* __restrict__ tab_out) {
   using U = typename Key<KT>::U;
   __shared__ U s[kMaxSamples];
   const Task t = tasks[blockIdx.x];
@@ -263,6 +302,36 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
   const int step = ns / B;
   for (int i = threadIdx.x; i < B - 1; i += THREADS) spl[i] = s[(i + 1) * step - 1];
   for (int j = 1 + threadIdx.x; j < B; j += THREADS) tree[j] = s[(eytz_inorder(j, logb) + 1) * step - 1];
+  // prefilter table over [spl[0], spl[B-2]] (the splitter of rank i is s[(i + 1) * step - 1])
+  const U lo = s[step - 1], hi = s[(B - 1) * step - 1];
+  const U range = hi - lo;
+  const int bits = range == 0 ? 0 : (int)(8 * sizeof(U)) - (sizeof(U) == 4 ? __clz((uint32_t)range) : __clzll((uint64_t)range));
+  const int shift = bits > kPrefBits ? bits - kPrefBits : 0;
+  const int nent = (int)(range >> shift) + 1;
+  if (threadIdx.x == 0) {
+    Pref<U> pf;
+    pf.lo = lo;
+    pf.hi = hi;
+    pf.shift = shift;
+    pf.nent = nent;
+    pref_out[blockIdx.x] = pf;
+  }
+  uint32_t* tab = tab_out + (size_t)blockIdx.x * kPrefEntries;
+  for (int k = threadIdx.x; k < nent; k += THREADS) {
+    const U first = lo + ((U)k << shift);
+    const U last = k == nent - 1 ? hi : first + (((U)1 << shift) - 1);
+    int a = 0, c = B - 1;  // #splitters < first: lower bound over spl[0..B-2]
+    while (a < c) {
+      const int m = (a + c) >> 1;
+      if (s[(m + 1) * step - 1] < first) a = m + 1; else c = m;
+    }
+    int a2 = 0, c2 = B - 1;  // #splitters <= last: upper bound
+    while (a2 < c2) {
+      const int m = (a2 + c2) >> 1;
+      if (s[(m + 1) * step - 1] <= last) a2 = m + 1; else c2 = m;
+    }
+    tab[k] = (uint32_t)a | ((uint32_t)a2 << 16);
+  }
 }
 
 // Loads the task's tree and splitters into shared memory.
@@ -275,22 +344,29 @@ __device__ __forceinline__ void load_splitters(U* s_tree, U* s_spl, const U* tre
 }
 
 // ================================================================== count
-// One CTA per chunk.  Tiles of TILE codes stream into STAGES shared buffers by bulk copy (the
-// ragged <16-byte edges of each tile are classified straight from global memory); every code is
-// classified and counted in a shared histogram, written to counts[chunk][bin] at the end.
+// One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE codes that stream
+// into STAGES shared buffers by bulk copy; elements of a window outside the chunk are masked
+// (only the first and last window have any), and the last window's sub-16-byte tail is
+// classified straight from global memory.  Every code is classified and counted in a shared
+// histogram, written to counts[chunk][bin] at the end.
 template <int KT, int THREADS, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
              const int32_t* __restrict__ task_logb, const typename Key<KT>::U* __restrict__ keys,
              const typename Key<KT>::U* __restrict__ tmp, const typename Key<KT>::U* __restrict__ tree_g,
-             const typename Key<KT>::U* __restrict__ spl_g, uint32_t* __restrict__ counts, Counters* ctr) {
+             const typename Key<KT>::U* __restrict__ spl_g, const Pref<typename Key<KT>::U>* __restrict__ pref_g,
+             const uint32_t* __restrict__ tab_g, uint32_t* __restrict__ counts, Counters* ctr) {
   using U = typename Key<KT>::U;
   constexpr int KS = sizeof(U);
-  constexpr int BUF_BYTES = TILE * KS + 16;
+  constexpr int VEC = 16 / KS;                // codes per 16-byte vector
+  constexpr int NV = TILE / VEC / THREADS;    // vectors per thread per window
+  static_assert(TILE % (VEC * THREADS) == 0, "window must split evenly into vectors");
+  constexpr int BUF_BYTES = TILE * KS;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[STAGES];
   __shared__ U s_tree[kBMax], s_spl[kBMax];
   __shared__ uint32_t hist[kBinsMax];
+  __shared__ uint32_t s_tab[kPrefEntries];
 
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
@@ -298,6 +374,8 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const int B = 1 << logb;
   const int nb = 2 * B;
   load_splitters(s_tree, s_spl, tree_g + (size_t)c.task * kBMax, spl_g + (size_t)c.task * kBMax, B);
+  const Pref<U> pf = pref_g[c.task];
+  for (int k = threadIdx.x; k < pf.nent; k += THREADS) s_tab[k] = tab_g[(size_t)c.task * kPrefEntries + k];
   for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&bars[i], 1);
@@ -307,16 +385,17 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const U* src = t.buf == kBufKeys ? keys : tmp;
   const bool enc = t.enc != 0;
   const int64_t cb = c.begin, ce = c.begin + c.size;
-  const int ntiles = (c.size + TILE - 1) / TILE;
+  const int64_t a0 = cb - cb % VEC;  // first window starts 16-byte aligned
+  const int ntiles = (int)((ce - a0 + TILE - 1) / TILE);
   auto buf = [&](int stg) { return reinterpret_cast<U*>(smem + (size_t)stg * BUF_BYTES); };
   auto issue = [&](int tile) {
-    const int64_t s0 = cb + (int64_t)tile * TILE;
-    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
-    const TileGeom<KS> g(s0, e0);
+    const int64_t ws = a0 + (int64_t)tile * TILE;
+    const int64_t we = ws + TILE < ce ? ws + TILE : ce;
+    const int64_t wa = we - we % VEC;
     const int stg = tile % STAGES;
-    const uint32_t bytes = g.bulk_bytes();
+    const uint32_t bytes = (uint32_t)((wa - ws) * KS);
     mbar_arrive_expect_tx(&bars[stg], bytes);
-    if (bytes) bulk_g2s(buf(stg) + (g.as - g.s_al), src + g.as, bytes, &bars[stg]);
+    if (bytes) bulk_g2s(buf(stg), src + ws, bytes, &bars[stg]);
   };
   if (threadIdx.x == 0)
     for (int i = 0; i < STAGES && i < ntiles; ++i) issue(i);
@@ -324,35 +403,43 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   bool failed = false;
   with_logb(logb, [&](auto LB) {
     constexpr int L = decltype(LB)::value;
+    auto count_one = [&](U x) {
+      atomicAdd(&hist[classify_fast<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl, s_tab, pf)], 1u);
+    };
     for (int tile = 0; tile < ntiles; ++tile) {
       const int stg = tile % STAGES;
-      const int64_t s0 = cb + (int64_t)tile * TILE;
-      const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
-      const TileGeom<KS> g(s0, e0);
+      const int64_t ws = a0 + (int64_t)tile * TILE;
+      const int64_t we = ws + TILE < ce ? ws + TILE : ce;
+      const int64_t wa = we - we % VEC;
       const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
       parity ^= 1u << stg;
       if (!__syncthreads_and(ok)) { failed = true; break; }
-      const U* bp = buf(stg);
-      const int k0 = (int)(g.as - g.s_al), k1 = (int)(g.ae - g.s_al);
-      constexpr int ILP = 4;
-      int k = k0 + threadIdx.x;
-      for (; k + (ILP - 1) * THREADS < k1; k += ILP * THREADS) {
-        int bin[ILP];
+      const uint4* bp = reinterpret_cast<const uint4*>(buf(stg));
+      if (ws >= cb && ws + TILE <= ce) {  // interior window: every element valid
 #pragma unroll
-        for (int q = 0; q < ILP; ++q) {
-          const U x = bp[k + q * THREADS];
-          bin[q] = classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl);
+        for (int q = 0; q < NV; ++q) {
+          U v[VEC];
+          *reinterpret_cast<uint4*>(v) = bp[threadIdx.x + q * THREADS];
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) count_one(v[i]);
         }
+      } else {
+        const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(wa - ws);
 #pragma unroll
-        for (int q = 0; q < ILP; ++q) atomicAdd(&hist[bin[q]], 1u);
-      }
-      for (; k < k1; k += THREADS) {
-        const U x = bp[k];
-        atomicAdd(&hist[classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
-      }
-      if ((int)threadIdx.x < g.head + g.tail) {
-        const U x = src[g.edge(s0, threadIdx.x)];
-        atomicAdd(&hist[classify_t<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+        for (int q = 0; q < NV; ++q) {
+          const int vi = threadIdx.x + q * THREADS;
+          if (vi * VEC >= k1) break;
+          U v[VEC];
+          *reinterpret_cast<uint4*>(v) = bp[vi];
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) {
+            const int k = vi * VEC + i;
+            if (k >= k0 && k < k1) count_one(v[i]);
+          }
+        }
+        // sub-16-byte tail of the chunk, straight from global memory
+        const int64_t g = (wa > cb ? wa : cb) + threadIdx.x;
+        if (g < we) count_one(src[g]);
       }
       __syncthreads();  // this stage's buffer is consumed
       if (threadIdx.x == 0 && tile + STAGES < ntiles) {
@@ -409,9 +496,11 @@ scan_kernel(const int32_t* __restrict__ task_logb, const int32_t* __restrict__ t
 }
 
 // ================================================================== scatter
-// One CTA per chunk, tiles of TILE elements double-buffered in shared memory by bulk copy.
-// Per tile: classify every code, rank it inside its bin with a shared atomic, scan the bin
-// counts, then stage the tile in place grouped by bin (codes and values), and write each bin's
+// One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE elements,
+// double-buffered in shared memory by bulk copy (the last window's sub-16-byte tail is fetched
+// with plain loads a tile ahead and stored before use); elements outside the chunk are masked.
+// Per window: classify every code, rank it inside its bin with a shared atomic, scan the bin
+// counts, stage the window in place grouped by bin (codes and values), then write each bin's
 // run to its next free slots in the destination buffer (coalesced within runs).  Keys of an
 // equality bin written to the key buffer are final and are decoded on the way out.
 template <int KT, int VB, int THREADS, int TILE>
@@ -420,23 +509,29 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
                const int32_t* __restrict__ task_logb, typename Key<KT>::U* __restrict__ keys,
                typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
                typename Val<VB>::T* __restrict__ tmpv, const typename Key<KT>::U* __restrict__ tree_g,
-               const typename Key<KT>::U* __restrict__ spl_g, const uint32_t* __restrict__ offsets,
-               Counters* ctr) {
+               const typename Key<KT>::U* __restrict__ spl_g, const Pref<typename Key<KT>::U>* __restrict__ pref_g,
+               const uint32_t* __restrict__ tab_g, const uint32_t* __restrict__ offsets, Counters* ctr) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
   constexpr int KS = sizeof(U);
-  constexpr int VS = VB ? VB : 4;
-  constexpr int ITEMS = TILE / THREADS;
-  constexpr int KBUF = TILE * KS + 16;
-  constexpr int VBUF = VB ? TILE * VS + 16 : 0;
+  constexpr int VS = VB ? VB : KS;
+  constexpr int VK = 16 / KS;                       // codes per 16-byte vector
+  constexpr int VV = 16 / VS;                       // values per 16-byte vector
+  constexpr int VA = VK > VV ? VK : VV;             // window alignment (elements)
+  constexpr int NV = TILE / VK / THREADS;           // code vectors per thread
+  constexpr int ITEMS = NV * VK;
+  static_assert(TILE % (VK * THREADS) == 0 && TILE % VA == 0, "window must split evenly");
+  constexpr int KBUF = TILE * KS;
+  constexpr int VBUF = VB ? TILE * VS : 0;
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* stage_b = reinterpret_cast<uint16_t*>(smem + 2 * (KBUF + VBUF));
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ U s_tree[kBMax], s_spl[kBMax];
-  __shared__ uint32_t hist[kBinsMax];     // per-tile counts, then tile bin starts
+  __shared__ uint32_t hist[kBinsMax];     // per-window counts, then window bin starts
   __shared__ uint32_t cursor[kBinsMax];   // next write offset per bin (task-relative)
-  __shared__ uint32_t gbase[kBinsMax];    // cursor - tile start, per bin
+  __shared__ uint32_t gbase[kBinsMax];    // cursor - window start, per bin
   __shared__ uint32_t wtmp[THREADS / 32 + 1];
+  __shared__ uint32_t s_tab[kPrefEntries];
 
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
@@ -448,6 +543,8 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
     cursor[b] = offsets[(size_t)blockIdx.x * kBinsMax + b];
     hist[b] = 0;
   }
+  const Pref<U> pf = pref_g[c.task];
+  for (int k = threadIdx.x; k < pf.nent; k += THREADS) s_tab[k] = tab_g[(size_t)c.task * kPrefEntries + k];
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -463,34 +560,34 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const bool dst_is_keys = !from_keys;
   const bool enc = t.enc != 0;
   const int64_t cb = c.begin, ce = c.begin + c.size;
-  const int ntiles = (c.size + TILE - 1) / TILE;
+  const int64_t a0 = cb - cb % VA;
+  const int ntiles = (int)((ce - a0 + TILE - 1) / TILE);
   auto kbuf = [&](int stg) { return reinterpret_cast<U*>(smem + (size_t)stg * KBUF); };
   auto vbuf = [&](int stg) { return reinterpret_cast<V*>(smem + 2 * (size_t)KBUF + (size_t)stg * VBUF); };
 
-  // ragged edge elements are fetched at issue time into registers of a few threads
-  // (threads 0..7: keys, 32..39: values) and stored into the buffer before the tile is used
+  // sub-16-byte tails (fewer than VK codes / VV values) are fetched at issue time into
+  // registers of threads 0..VK-2 (codes) and 32..32+VV-2 (values), stored before use
   U pend_k0 = U(0), pend_k1 = U(0);
   V pend_v0 = V(0), pend_v1 = V(0);
   auto issue = [&](int tile) {
     const int stg = tile & 1;
-    const int64_t s0 = cb + (int64_t)tile * TILE;
-    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
-    const TileGeom<KS> gk(s0, e0);
-    const TileGeom<VS> gv(s0, e0);
+    const int64_t ws = a0 + (int64_t)tile * TILE;
+    const int64_t we = ws + TILE < ce ? ws + TILE : ce;
+    const int64_t wk = we - we % VK, wv = we - we % VV;
     if (threadIdx.x == 0) {
-      const uint32_t kb = gk.bulk_bytes(), vb = VB ? gv.bulk_bytes() : 0u;
+      const uint32_t kb = (uint32_t)((wk - ws) * KS), vb = VB ? (uint32_t)((wv - ws) * VS) : 0u;
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&bars[stg], kb + vb);
-      if (kb) bulk_g2s(kbuf(stg) + (gk.as - gk.s_al), srck + gk.as, kb, &bars[stg]);
-      if (VB && vb) bulk_g2s(vbuf(stg) + (gv.as - gv.s_al), srcv + gv.as, vb, &bars[stg]);
+      if (kb) bulk_g2s(kbuf(stg), srck + ws, kb, &bars[stg]);
+      if (VB && vb) bulk_g2s(vbuf(stg), srcv + ws, vb, &bars[stg]);
     }
     const int tid = threadIdx.x;
-    if (tid < 8 && tid < gk.head + gk.tail) {
-      const U x = srck[gk.edge(s0, tid)];
+    if (tid < VK && wk + tid < we) {
+      const U x = srck[wk + tid];
       if (stg) pend_k1 = x; else pend_k0 = x;
     }
-    if (VB && tid >= 32 && tid < 40 && tid - 32 < gv.head + gv.tail) {
-      const V x = srcv[gv.edge(s0, tid - 32)];
+    if (VB && tid >= 32 && tid < 32 + VV && wv + (tid - 32) < we) {
+      const V x = srcv[wv + (tid - 32)];
       if (stg) pend_v1 = x; else pend_v0 = x;
     }
   };
@@ -499,74 +596,81 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 
   uint32_t parity = 0;
   bool failed = false;
-  for (int tile = 0; tile < ntiles; ++tile) {
-    const int stg = tile & 1;
-    const int64_t s0 = cb + (int64_t)tile * TILE;
-    const int64_t e0 = s0 + TILE < ce ? s0 + TILE : ce;
-    const int cnt = (int)(e0 - s0);
-    const TileGeom<KS> gk(s0, e0);
-    const TileGeom<VS> gv(s0, e0);
-    U* bk = kbuf(stg);
-    V* bv = VB ? vbuf(stg) : nullptr;
-    {
-      const int tid = threadIdx.x;
-      if (tid < 8 && tid < gk.head + gk.tail) bk[gk.edge(s0, tid) - gk.s_al] = stg ? pend_k1 : pend_k0;
-      if (VB && tid >= 32 && tid < 40 && tid - 32 < gv.head + gv.tail)
-        bv[gv.edge(s0, tid - 32) - gv.s_al] = stg ? pend_v1 : pend_v0;
-    }
-    const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
-    parity ^= 1u << stg;
-    if (!__syncthreads_and(ok)) { failed = true; break; }
+  with_logb(logb, [&](auto LB) {
+    constexpr int L = decltype(LB)::value;
+    for (int tile = 0; tile < ntiles; ++tile) {
+      const int stg = tile & 1;
+      const int64_t ws = a0 + (int64_t)tile * TILE;
+      const int64_t we = ws + TILE < ce ? ws + TILE : ce;
+      const int64_t wk = we - we % VK, wv = we - we % VV;
+      const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(we - ws);  // valid buffer range
+      const int cnt = k1 - k0;
+      const bool full = k0 == 0 && k1 == TILE;
+      U* bk = kbuf(stg);
+      V* bv = VB ? vbuf(stg) : nullptr;
+      {
+        const int tid = threadIdx.x;
+        if (tid < VK && wk + tid < we) bk[wk - ws + tid] = stg ? pend_k1 : pend_k0;
+        if (VB && tid >= 32 && tid < 32 + VV && wv + (tid - 32) < we) bv[wv - ws + (tid - 32)] = stg ? pend_v1 : pend_v0;
+      }
+      const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
+      parity ^= 1u << stg;
+      if (!__syncthreads_and(ok)) { failed = true; break; }
 
-    U code[ITEMS];
-    V val[ITEMS];
-    uint32_t packed[ITEMS];  // bin << 16 | rank inside the bin
-    with_logb(logb, [&](auto LB) {
-      constexpr int L = decltype(LB)::value;
+      U code[ITEMS];
+      V val[ITEMS];
+      uint32_t packed[ITEMS];  // bin << 16 | rank inside the bin; 0xFFFFFFFF for masked slots
 #pragma unroll
-      for (int e = 0; e < ITEMS; ++e) {
-        const int i = e * THREADS + threadIdx.x;
-        if (i < cnt) {
-          const U x = bk[gk.off + i];
-          code[e] = enc ? x : Key<KT>::enc(x);
-          if (VB) val[e] = bv[gv.off + i];
-          const int bin = classify_t<L>(code[e], s_tree, s_spl);
-          packed[e] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
+      for (int q = 0; q < NV; ++q) {
+        const int vi = threadIdx.x + q * THREADS;
+        U v[VK];
+        *reinterpret_cast<uint4*>(v) = reinterpret_cast<const uint4*>(bk)[vi];
+#pragma unroll
+        for (int i = 0; i < VK; ++i) {
+          const int e = q * VK + i;
+          const int k = vi * VK + i;
+          const bool valid = full || (k >= k0 && k < k1);
+          code[e] = enc ? v[i] : Key<KT>::enc(v[i]);
+          if (VB) val[e] = bv[k];
+          if (valid) {
+            const int bin = classify_fast<L>(code[e], s_tree, s_spl, s_tab, pf);
+            packed[e] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
+          } else {
+            packed[e] = 0xFFFFFFFFu;
+          }
         }
       }
-    });
-    __syncthreads();
-    block_exclusive_scan<THREADS>(hist, hist, nb, wtmp);  // hist := tile start of each bin
-    for (int b = threadIdx.x; b < nb; b += THREADS) {
-      const uint32_t next = (b + 1 < nb) ? hist[b + 1] : (uint32_t)cnt;
-      gbase[b] = cursor[b] - hist[b];
-      cursor[b] += next - hist[b];
-    }
-    // stage in place: every thread has read its codes from the buffer (scan barriers above)
-#pragma unroll
-    for (int e = 0; e < ITEMS; ++e) {
-      const int i = e * THREADS + threadIdx.x;
-      if (i < cnt) {
-        const uint32_t bin = packed[e] >> 16;
-        const uint32_t p = hist[bin] + (packed[e] & 0xFFFFu);
-        bk[p] = code[e];
-        if (VB) bv[p] = val[e];
-        stage_b[p] = (uint16_t)bin;
+      __syncthreads();
+      block_exclusive_scan<THREADS>(hist, hist, nb, wtmp);  // hist := window start of each bin
+      for (int b = threadIdx.x; b < nb; b += THREADS) {
+        const uint32_t next = (b + 1 < nb) ? hist[b + 1] : (uint32_t)cnt;
+        gbase[b] = cursor[b] - hist[b];
+        cursor[b] += next - hist[b];
       }
+      // stage in place: every thread has read its codes from the buffer (scan barriers above)
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        if (packed[e] != 0xFFFFFFFFu) {
+          const uint32_t bin = packed[e] >> 16;
+          const uint32_t p = hist[bin] + (packed[e] & 0xFFFFu);
+          bk[p] = code[e];
+          if (VB) bv[p] = val[e];
+          stage_b[p] = (uint16_t)bin;
+        }
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < cnt; i += THREADS) {
+        const int b = stage_b[i];
+        const uint32_t o = gbase[b] + (uint32_t)i;
+        const U k = bk[i];
+        dstk[o] = (dst_is_keys && (b & 1)) ? Key<KT>::dec(k) : k;  // equality bin: final, decode
+        if (VB) dstv[o] = bv[i];
+      }
+      __syncthreads();  // buffer, stage_b and hist are free again
+      for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+      if (tile + 2 < ntiles) issue(tile + 2);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += THREADS) {
-      const int b = stage_b[i];
-      const uint32_t o = gbase[b] + (uint32_t)i;
-      U k = bk[i];
-      if (dst_is_keys && (b & 1)) k = Key<KT>::dec(k);  // equality bin: final, decode now
-      dstk[o] = k;
-      if (VB) dstv[o] = bv[i];
-    }
-    __syncthreads();  // buffer, stage_b and hist are free again
-    for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
-    if (tile + 2 < ntiles) issue(tile + 2);
-  }
+  });
   if (failed && threadIdx.x == 0) {
     atomicAdd(&ctr->timeout, 1ull);
     for (int i = 0; i < 2; ++i) mbar_wait_bounded(&bars[i], (parity >> i) & 1u);
@@ -670,11 +774,21 @@ __device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
       for (int i = 0; i < N; ++i) {
         const int l = i ^ j;
         if (l > i) {
-          const bool up = (i & kk) == 0;
-          const bool gt = precedes<WITH_IDX>(k[l], x[l], k[i], x[i]);  // (k[i],x[i]) > (k[l],x[l])
-          if (gt == up) {
-            const U t = k[i]; k[i] = k[l]; k[l] = t;
-            if (WITH_IDX) { const uint32_t y = x[i]; x[i] = x[l]; x[l] = y; }
+          const bool up = (i & kk) == 0;  // compile-time direction
+          if (WITH_IDX) {
+            const bool gt = precedes<true>(k[l], x[l], k[i], x[i]);
+            const bool sw = gt == up;
+            const U a = k[i], b = k[l];
+            const uint32_t ya = x[i], yb = x[l];
+            k[i] = sw ? b : a;
+            k[l] = sw ? a : b;
+            x[i] = sw ? yb : ya;
+            x[l] = sw ? ya : yb;
+          } else {
+            const U a = k[i], b = k[l];
+            const U lo = a < b ? a : b, hi = a < b ? b : a;
+            k[i] = up ? lo : hi;
+            k[l] = up ? hi : lo;
           }
         }
       }
@@ -746,32 +860,44 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
       const int g = pos & ~(2 * R - 1);  // first element of the pair of runs
       const int d = pos - g;             // this thread's diagonal inside the pair
       const int a0 = g, b0 = g + R;
+      // merge-path split: the number of A elements among the first d outputs (ties take A)
       int lo = d > R ? d - R : 0;
       int hi = d < R ? d : R;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int pa = pad_idx<U>(a0 + mid), pb = pad_idx<U>(b0 + d - 1 - mid);
-        if (!precedes<W>(sk[pb], W ? si[pb] : 0u, sk[pa], W ? si[pa] : 0u)) lo = mid + 1;
-        else hi = mid;
+      for (int span = R; span > 0; span >>= 1) {  // log2(R) + 1 halvings suffice
+        if (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          const int pa = pad_idx<U>(a0 + mid), pb = pad_idx<U>(b0 + d - 1 - mid);
+          if (!precedes<W>(sk[pb], W ? si[pb] : 0u, sk[pa], W ? si[pa] : 0u)) lo = mid + 1;
+          else hi = mid;
+        }
       }
       int ai = lo, bi = d - lo;
-      U ka = k[0], kb = k[0];
+      U ka, kb;
       uint32_t xa = 0, xb = 0;
-      if (ai < R) { const int p = pad_idx<U>(a0 + ai); ka = sk[p]; if (W) xa = si[p]; }
-      if (bi < R) { const int p = pad_idx<U>(b0 + bi); kb = sk[p]; if (W) xb = si[p]; }
+      {
+        const int pa = pad_idx<U>(a0 + (ai < R ? ai : 0)), pb = pad_idx<U>(b0 + (bi < R ? bi : 0));
+        ka = sk[pa];
+        kb = sk[pb];
+        if (W) { xa = si[pa]; xb = si[pb]; }
+      }
+      // branch-free serial merge of ITEMS outputs: one shared load per output
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
         const bool a_ok = ai < R, b_ok = bi < R;
         const bool take_a = a_ok && (!b_ok || !precedes<W>(kb, xb, ka, xa));
         k[e] = take_a ? ka : kb;
         x[e] = take_a ? xa : xb;
-        if (take_a) {
-          ++ai;
-          if (ai < R) { const int p = pad_idx<U>(a0 + ai); ka = sk[p]; if (W) xa = si[p]; }
-        } else {
-          ++bi;
-          if (bi < R) { const int p = pad_idx<U>(b0 + bi); kb = sk[p]; if (W) xb = si[p]; }
-        }
+        ai += take_a ? 1 : 0;
+        bi += take_a ? 0 : 1;
+        const int nidx = take_a ? a0 + ai : b0 + bi;
+        const bool nok = take_a ? ai < R : bi < R;
+        const int p = pad_idx<U>(nok ? nidx : g);
+        const U nk = sk[p];
+        const uint32_t nx = W ? si[p] : 0u;
+        ka = take_a ? nk : ka;
+        kb = take_a ? kb : nk;
+        xa = take_a ? nx : xa;
+        xb = take_a ? xb : nx;
       }
     }
   }

@@ -53,6 +53,8 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
   L.tree = take((size_t)L.round_cap * kBMax * ks);
   L.spl = take((size_t)L.round_cap * kBMax * ks);
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
+  L.pref = take((size_t)L.round_cap * 32);
+  L.tab = take((size_t)L.round_cap * kPrefEntries * sizeof(uint32_t));
   L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
@@ -68,12 +70,12 @@ struct Shape {
   static constexpr int kScatterThreads = 512;
   static constexpr int kScatterTile = (KS + VB) <= 4 ? 8192 : ((KS + VB) <= 8 ? 4096 : 2048);
   static constexpr size_t kScatterSmem =
-      2 * ((size_t)kScatterTile * KS + 16 + (VB ? (size_t)kScatterTile * VB + 16 : 0)) + (size_t)kScatterTile * 2;
+      2 * ((size_t)kScatterTile * KS + (size_t)kScatterTile * VB) + (size_t)kScatterTile * 2;
   // count: 512 threads, four 16 KiB tiles in flight
   static constexpr int kCountThreads = 512;
   static constexpr int kCountTile = 16384 / KS;
-  static constexpr int kCountStages = 4;
-  static constexpr size_t kCountSmem = (size_t)kCountStages * (kCountTile * KS + 16);
+  static constexpr int kCountStages = 3;
+  static constexpr size_t kCountSmem = (size_t)kCountStages * kCountTile * KS;
   static constexpr int kSampleThreads = 512;
   // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
   // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits)
@@ -126,6 +128,8 @@ class PlainSorter {
     tree_ = reinterpret_cast<U*>(ws + L_.tree);
     spl_ = reinterpret_cast<U*>(ws + L_.spl);
     children_ = reinterpret_cast<uint2*>(ws + L_.children);
+    pref_ = reinterpret_cast<Pref<U>*>(ws + L_.pref);
+    tab_ = reinterpret_cast<uint32_t*>(ws + L_.tab);
     base_items_ = reinterpret_cast<Item*>(ws + L_.base_items);
     copy_items_ = reinterpret_cast<Item*>(ws + L_.copy_items);
     fb_items_ = reinterpret_cast<Item*>(ws + L_.fb_items);
@@ -187,6 +191,8 @@ class PlainSorter {
   Chunk* chunks_;
   uint32_t* counts_;
   uint2* children_;
+  Pref<U>* pref_;
+  uint32_t* tab_;
   Item *base_items_, *copy_items_, *fb_items_;
   cudaStream_t st_;
 
@@ -314,14 +320,14 @@ class PlainSorter {
     {
       LaunchScope ls("sample", st_, 0.0);
       sample_kernel<KT, S::kSampleThreads><<<nt, S::kSampleThreads, 0, st_>>>(
-          tasks_, d_logb, oversample, keys_, tmpk_, tree_, spl_);
+          tasks_, d_logb, oversample, keys_, tmpk_, tree_, spl_, pref_, tab_);
     }
     PDQ_LAUNCHED("sample");
     {
       LaunchScope ls("count", st_, (double)total * KS);
       count_kernel<KT, S::kCountThreads, S::kCountTile, S::kCountStages>
           <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, d_logb, keys_, tmpk_, tree_,
-                                                              spl_, counts_, ctr_);
+                                                              spl_, pref_, tab_, counts_, ctr_);
     }
     PDQ_LAUNCHED("count");
     {
@@ -333,7 +339,7 @@ class PlainSorter {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
       scatter_kernel<KT, VB, S::kScatterThreads, S::kScatterTile>
           <<<nchunks, S::kScatterThreads, S::kScatterSmem, st_>>>(
-              chunks_, tasks_, d_logb, keys_, vals_, tmpk_, tmpv_, tree_, spl_, counts_, ctr_);
+              chunks_, tasks_, d_logb, keys_, vals_, tmpk_, tmpv_, tree_, spl_, pref_, tab_, counts_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
     {
