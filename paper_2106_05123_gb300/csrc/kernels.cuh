@@ -749,7 +749,8 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
 // values) starts 16-byte aligned.
 template <int KS>
 __host__ __device__ constexpr int base_sort_pcap(int cap) {
-  return (cap + cap / (KS == 4 ? 32 : 16) + 1 + 3) / 4 * 4;
+  // + 32 slack elements: read-ahead one past a run and the padding of the last thread
+  return (cap + 32 + (cap + 32) / (KS == 4 ? 32 : 16) + 1 + 3) / 4 * 4;
 }
 
 template <class U>
@@ -815,13 +816,12 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
   const Item it = items[blockIdx.x];
   const int m = (int)it.size;
   const int tid = threadIdx.x;
-  // active threads: a power of two covering m
-  int na = 1;
-  while (na * ITEMS < m) na <<= 1;
+  // P: m rounded up to whole threads (at most ITEMS-1 padding elements); runs may be ragged
+  const int na = (m + ITEMS - 1) / ITEMS;
   const int P = na * ITEMS;
   const U* srck = (it.buf == kBufKeys ? keys : tmpk) + it.begin;
   const V* srcv = W ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
-  for (int i = tid; i < P; i += THREADS) {
+  for (int i = tid; i < P + ITEMS; i += THREADS) {  // ITEMS slack slots: harmless read-ahead
     U c = ~U(0);
     if (i < m) {
       const U x = srck[i];
@@ -860,9 +860,11 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
       const int g = pos & ~(2 * R - 1);  // first element of the pair of runs
       const int d = pos - g;             // this thread's diagonal inside the pair
       const int a0 = g, b0 = g + R;
+      const int la = min(R, P - g);                  // run A (may be the ragged last run)
+      const int lb = max(0, min(R, P - g - R));      // run B (may be short or empty)
       // merge-path split: the number of A elements among the first d outputs (ties take A)
-      int lo = d > R ? d - R : 0;
-      int hi = d < R ? d : R;
+      int lo = d > lb ? d - lb : 0;
+      int hi = d < la ? d : la;
       for (int span = R; span > 0; span >>= 1) {  // log2(R) + 1 halvings suffice
         if (lo < hi) {
           const int mid = (lo + hi) >> 1;
@@ -872,26 +874,19 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
         }
       }
       int ai = lo, bi = d - lo;
-      U ka, kb;
+      U ka = sk[pad_idx<U>(a0 + ai)], kb = sk[pad_idx<U>(b0 + bi)];
       uint32_t xa = 0, xb = 0;
-      {
-        const int pa = pad_idx<U>(a0 + (ai < R ? ai : 0)), pb = pad_idx<U>(b0 + (bi < R ? bi : 0));
-        ka = sk[pa];
-        kb = sk[pb];
-        if (W) { xa = si[pa]; xb = si[pb]; }
-      }
-      // branch-free serial merge of ITEMS outputs: one shared load per output
+      if (W) { xa = si[pad_idx<U>(a0 + ai)]; xb = si[pad_idx<U>(b0 + bi)]; }
+      // branch-free serial merge of ITEMS outputs: one shared load per output; a load one past
+      // the end of a run stays inside the array (slack) and is never selected
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
-        const bool a_ok = ai < R, b_ok = bi < R;
-        const bool take_a = a_ok && (!b_ok || !precedes<W>(kb, xb, ka, xa));
+        const bool take_a = ai < la && (bi >= lb || !precedes<W>(kb, xb, ka, xa));
         k[e] = take_a ? ka : kb;
         x[e] = take_a ? xa : xb;
         ai += take_a ? 1 : 0;
         bi += take_a ? 0 : 1;
-        const int nidx = take_a ? a0 + ai : b0 + bi;
-        const bool nok = take_a ? ai < R : bi < R;
-        const int p = pad_idx<U>(nok ? nidx : g);
+        const int p = pad_idx<U>(take_a ? a0 + ai : b0 + bi);
         const U nk = sk[p];
         const uint32_t nx = W ? si[p] : 0u;
         ka = take_a ? nk : ka;
