@@ -79,11 +79,14 @@ typedef struct {
   int32_t base_capacity;    /* largest bucket sorted in shared memory, 256..16384, power of 2 */
   int32_t bad_allowed;      /* >0: start value of the bad-split counter; -1: start at 0 */
   int32_t probe;            /* 0: default (probe on); -1: skip the sorted/reverse probe */
-  int32_t reserved[3];
+  int32_t wait_limit_us;    /* segmented path: bound of every device-side wait (0: 2 s) */
+  int32_t inject_wait;      /* test hook, segmented path: one CTA first waits on a flag nothing
+                               sets; with a short wait_limit_us the call returns PDQ_ERR_TIMEOUT */
+  int32_t seg_block;        /* segmented path: persistent kernel block size, 256 or 512 (default) */
 } pdq_tuning;
 
 /* Bytes of workspace the sort of n keys (and a payload of value_bytes, 0 for keys only) needs.
- * num_segments: 0 or 1 for the single-array calls; the segment count for pdq_sort_segmented.
+ * num_segments: 0 for the single-array calls; the segment count (>= 1) for pdq_sort_segmented.
  * Returns 0 for an unknown dtype or value_bytes. */
 size_t pdq_workspace_bytes(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes);
 
@@ -99,6 +102,22 @@ int pdq_sort_keys(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_ws, size
 int pdq_sort_pairs(void* d_keys, void* d_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
                    void* d_ws, size_t ws_bytes, void* cuda_stream, const pdq_tuning* tuning,
                    pdq_stats* stats);
+
+/* Sort num_segments independent segments [offsets[s], offsets[s+1]) of one array in a single
+ * call: segments go to size-binned device work queues served by one persistent kernel (each
+ * CTA sorts small segments in shared memory and partitions larger ones, pushing the parts back);
+ * the launch is captured in a CUDA graph that is reused while pointers and sizes repeat (this
+ * graph cache is the only memory the library allocates; host-side graph objects).  Segments
+ * above 2^20 keys use the plain multi-CTA path.
+ *   d_offsets: device int64 array of num_segments + 1 non-decreasing entries in [0, n]
+ *   n        : number of keys (offsets[num_segments] at most)
+ *   d_vals   : NULL with value_bytes 0, else the payload array
+ * Offsets outside [0, n] or decreasing give PDQ_ERR_ARG (detected on the device).
+ * A bounded wait that expires gives PDQ_ERR_TIMEOUT; the arrays then still hold a permutation
+ * of the input pairs. */
+int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_t* d_offsets,
+                       int64_t num_segments, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                       void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats);
 
 /* Host-buffer convenience form of pdq_sort_keys / pdq_sort_pairs: copies h_keys (and h_vals
  * when value_bytes > 0) into the caller's device buffers d_keys / d_vals, sorts them there and

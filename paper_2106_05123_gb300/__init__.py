@@ -5,8 +5,8 @@ provides device memory and streams.  The library must have been built (``__graft
 or ``python paper_2106_05123_gb300/_build.py``); there is no CPU fallback, and every call raises
 ``PdqError`` when the library or a CUDA device is missing.
 
-Names follow the C ABI: ``pdq_sort_keys``, ``pdq_sort_pairs``, ``pdq_sort_host``,
-``pdq_workspace_bytes``, ``pdq_reverse``.
+Names follow the C ABI: ``pdq_sort_keys``, ``pdq_sort_pairs``, ``pdq_sort_segmented``,
+``pdq_sort_host``, ``pdq_workspace_bytes``, ``pdq_reverse``, ``pdq_sort_keys_noalloc``.
 """
 
 from __future__ import annotations
@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("log2_buckets", ctypes.c_int32), ("oversample", ctypes.c_int32),
                 ("base_capacity", ctypes.c_int32), ("bad_allowed", ctypes.c_int32),
-                ("probe", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("probe", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
+                ("inject_wait", ctypes.c_int32), ("seg_block", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -77,6 +78,8 @@ def lib() -> ctypes.CDLL:
             L.pdq_sort_pairs.argtypes = [vp, vp, i32, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
             L.pdq_sort_pairs.restype = i32
             L.pdq_sort_host.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_segmented.argtypes = [vp, vp, i32, vp, i64, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_segmented.restype = i32
             L.pdq_sort_host.restype = i32
             L.pdq_sort_keys_noalloc.argtypes = [vp, i64, i32, vp, P(Stats)]
             L.pdq_sort_keys_noalloc.restype = i32
@@ -124,13 +127,14 @@ def _tuning(t) -> ctypes.POINTER(Tuning) | None:
     return ctypes.pointer(tt)
 
 
-def pdq_workspace_bytes(n: int, key_dtype, value_bytes: int = 0, num_segments: int = 1) -> int:
-    """Workspace bytes for a call; key_dtype is a torch dtype or a PDQ_* code."""
+def pdq_workspace_bytes(n: int, key_dtype, value_bytes: int = 0, num_segments: int = 0) -> int:
+    """Workspace bytes for a call; key_dtype is a torch dtype or a PDQ_* code; num_segments is
+    0 for the single-array calls and the segment count for pdq_sort_segmented."""
     code = key_dtype if isinstance(key_dtype, int) else key_dtype_code(key_dtype)
     return int(lib().pdq_workspace_bytes(int(n), int(num_segments), code, int(value_bytes)))
 
 
-def workspace_for(n: int, key_dtype: torch.dtype, value_bytes: int = 0, num_segments: int = 1,
+def workspace_for(n: int, key_dtype, value_bytes: int = 0, num_segments: int = 0,
                   device="cuda") -> torch.Tensor:
     """A uint8 device tensor large enough (and 256-byte aligned) for the call."""
     nbytes = pdq_workspace_bytes(n, key_dtype, value_bytes, num_segments)
@@ -151,7 +155,7 @@ def pdq_sort_keys(keys: torch.Tensor, workspace: torch.Tensor | None = None, tun
     _require_cuda(keys, "keys")
     dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
     n = keys.numel()
-    ws = workspace if workspace is not None else workspace_for(n, keys.dtype, 0, 1, keys.device)
+    ws = workspace if workspace is not None else workspace_for(n, dt, 0, 0, keys.device)
     st = Stats()
     _check(lib().pdq_sort_keys(keys.data_ptr(), n, dt, ws.data_ptr(), ws.numel(),
                                _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
@@ -168,10 +172,35 @@ def pdq_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, workspace: torch.Tens
     vb = vals.element_size()
     dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
     n = keys.numel()
-    ws = workspace if workspace is not None else workspace_for(n, keys.dtype, vb, 1, keys.device)
+    ws = workspace if workspace is not None else workspace_for(n, dt, vb, 0, keys.device)
     st = Stats()
     _check(lib().pdq_sort_pairs(keys.data_ptr(), vals.data_ptr(), vb, n, dt, ws.data_ptr(),
                                 ws.numel(), _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, vals: torch.Tensor | None = None,
+                       workspace: torch.Tensor | None = None, tuning=None, stream=None,
+                       key_dtype: int | None = None) -> dict:
+    """Sort every segment [offsets[s], offsets[s+1]) of ``keys`` (and ``vals``) in place in one
+    call; ``offsets`` is a CUDA int64 tensor of num_segments + 1 non-decreasing entries."""
+    _require_cuda(keys, "keys")
+    _require_cuda(offsets, "offsets")
+    if offsets.dtype != torch.int64:
+        raise PdqError(-1, "offsets must be int64")
+    if vals is not None:
+        _require_cuda(vals, "vals")
+        if vals.numel() != keys.numel():
+            raise PdqError(-1, "keys and vals differ in length")
+    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    vb = vals.element_size() if vals is not None else 0
+    n = keys.numel()
+    nseg = max(0, offsets.numel() - 1)
+    ws = workspace if workspace is not None else workspace_for(n, dt, vb, max(1, nseg), keys.device)
+    st = Stats()
+    _check(lib().pdq_sort_segmented(keys.data_ptr(), vals.data_ptr() if vals is not None else None, vb,
+                                    offsets.data_ptr(), nseg, n, dt, ws.data_ptr(), ws.numel(),
+                                    _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
     return st.as_dict()
 
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "graph_cache.h"
 #include "sort_api.h"
 
 namespace pdq {
@@ -64,6 +65,13 @@ void note_launch_end(const char* name, cudaStream_t s) {
 
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+void note_launch_count(int extra) { g_launches.fetch_add(extra, std::memory_order_relaxed); }
+
+GraphCache& graph_cache() {
+  static GraphCache* gc = new GraphCache();  // lives until exit (graph objects are host-side)
+  return *gc;
+}
+
 static void resolve_pending() {
   std::lock_guard<std::mutex> g(g_prof_mu);
   for (Pending& p : g_pending) {
@@ -107,6 +115,9 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
   d.base_cap = kBaseCapMax;
   d.bad_allowed = 0;
   d.probe = true;
+  d.wait_us = 0;
+  d.inject_wait = 0;
+  d.seg_block = 512;
   if (t) {
     if (t->log2_buckets) {
       if (t->log2_buckets < 1 || t->log2_buckets > kLogBMax)
@@ -126,6 +137,12 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
     }
     if (t->bad_allowed) d.bad_allowed = t->bad_allowed;
     if (t->probe < 0) d.probe = false;
+    if (t->wait_limit_us < 0) return set_error(PDQ_ERR_ARG, "tuning.wait_limit_us must be >= 0");
+    d.wait_us = t->wait_limit_us;
+    d.inject_wait = t->inject_wait != 0;
+    if (t->seg_block && t->seg_block != 256 && t->seg_block != 512)
+      return set_error(PDQ_ERR_ARG, "tuning.seg_block must be 256 or 512");
+    if (t->seg_block) d.seg_block = t->seg_block;
   }
   *out = d;
   return PDQ_OK;
@@ -140,6 +157,30 @@ static int dispatch_sort(int dt, const SortArgs& a, pdq_stats* st) {
     case PDQ_U64: return sort_impl<PDQ_U64, VB>(a, st);
     case PDQ_F32: return sort_impl<PDQ_F32, VB>(a, st);
     default: return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  }
+}
+
+template <int VB>
+static int dispatch_seg(int dt, const SegArgs& a, pdq_stats* st) {
+  switch (dt) {
+    case PDQ_I32: return seg_sort_impl<PDQ_I32, VB>(a, st);
+    case PDQ_U32: return seg_sort_impl<PDQ_U32, VB>(a, st);
+    case PDQ_I64: return seg_sort_impl<PDQ_I64, VB>(a, st);
+    case PDQ_U64: return seg_sort_impl<PDQ_U64, VB>(a, st);
+    case PDQ_F32: return seg_sort_impl<PDQ_F32, VB>(a, st);
+    default: return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  }
+}
+
+template <int VB>
+static size_t dispatch_seg_ws(int dt, int64_t n, int64_t nseg) {
+  switch (dt) {
+    case PDQ_I32: return seg_workspace_bytes_impl<PDQ_I32, VB>(n, nseg);
+    case PDQ_U32: return seg_workspace_bytes_impl<PDQ_U32, VB>(n, nseg);
+    case PDQ_I64: return seg_workspace_bytes_impl<PDQ_I64, VB>(n, nseg);
+    case PDQ_U64: return seg_workspace_bytes_impl<PDQ_U64, VB>(n, nseg);
+    case PDQ_F32: return seg_workspace_bytes_impl<PDQ_F32, VB>(n, nseg);
+    default: return 0;
   }
 }
 
@@ -193,8 +234,15 @@ using namespace pdq;
 extern "C" {
 
 size_t pdq_workspace_bytes(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes) {
-  (void)num_segments;
-  if (n < 0) return 0;
+  if (n < 0 || num_segments < 0) return 0;
+  if (num_segments > 0) {
+    switch (value_bytes) {
+      case 0: return dispatch_seg_ws<0>(key_dtype, n, num_segments);
+      case 4: return dispatch_seg_ws<4>(key_dtype, n, num_segments);
+      case 8: return dispatch_seg_ws<8>(key_dtype, n, num_segments);
+      default: return 0;
+    }
+  }
   switch (value_bytes) {
     case 0: return dispatch_ws<0>(key_dtype, n);
     case 4: return dispatch_ws<4>(key_dtype, n);
@@ -240,6 +288,42 @@ int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dt
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("D2H: ") + cudaGetErrorString(e));
   return PDQ_OK;
+}
+
+int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_t* d_offsets,
+                       int64_t num_segments, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                       void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats) {
+  g_last_error.clear();
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  const int kb = key_bytes(key_dtype);
+  if (!kb) return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
+  if (n < 0 || n >= (int64_t(1) << 32) || num_segments < 0)
+    return set_error(PDQ_ERR_ARG, "n must be in [0, 2^32) and num_segments >= 0");
+  if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8)
+    return set_error(PDQ_ERR_ARG, "value_bytes must be 0, 4 or 8");
+  if (num_segments == 0 || n <= 1) return PDQ_OK;
+  if (!d_offsets || ((uintptr_t)d_offsets % 8)) return set_error(PDQ_ERR_ARG, "offsets pointer null or misaligned");
+  if (!d_keys || ((uintptr_t)d_keys % 16)) return set_error(PDQ_ERR_ARG, "keys pointer null or not 16-byte aligned");
+  if (value_bytes && (!d_vals || ((uintptr_t)d_vals % 16)))
+    return set_error(PDQ_ERR_ARG, "values pointer null or not 16-byte aligned");
+  if (!d_ws || ((uintptr_t)d_ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
+  SegArgs a;
+  a.keys = d_keys;
+  a.vals = d_vals;
+  a.offsets = d_offsets;
+  a.nseg = num_segments;
+  a.n = n;
+  a.ws = d_ws;
+  a.ws_bytes = ws_bytes;
+  a.stream = static_cast<cudaStream_t>(cuda_stream);
+  a.num_sms = num_sms();
+  int rc = make_tuning(tuning, &a.tune);
+  if (rc) return rc;
+  switch (value_bytes) {
+    case 0: return dispatch_seg<0>(key_dtype, a, stats);
+    case 4: return dispatch_seg<4>(key_dtype, a, stats);
+    default: return dispatch_seg<8>(key_dtype, a, stats);
+  }
 }
 
 const char* pdq_last_error(void) { return g_last_error.c_str(); }

@@ -134,6 +134,7 @@ __host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
 void note_launch(const char* name, cudaStream_t s, double bytes);    // before a launch
 void note_launch_end(const char* name, cudaStream_t s);              // after a launch
 int64_t launches_so_far();
+void note_launch_count(int extra);                                   // kernels inside a graph launch
 
 struct LaunchScope {
   const char* name;

@@ -1,3 +1,5 @@
-// Instantiation of the plain sort path for PDQ_F32 keys (keys only, 4-byte and 8-byte payloads).
+// Instantiation of the plain sort path for PDQ_F32 keys (keys only, 4-byte and 8-byte payloads; plain and segmented).
+#include "seg_impl.cuh"
 #include "sort_impl.cuh"
 PDQ_INSTANTIATE(PDQ_F32)
+PDQ_INSTANTIATE_SEG(PDQ_F32)

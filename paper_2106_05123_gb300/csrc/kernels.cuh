@@ -797,23 +797,24 @@ __device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
   }
 }
 
+// The whole sort of one item by one CTA (blockDim.x == THREADS); `smem` holds
+// base_sort_smem<KS, VB, THREADS, ITEMS>() bytes, 16-byte aligned.
 template <int KT, int VB, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
-base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict__ keys,
-                 typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
-                 typename Val<VB>::T* __restrict__ tmpv, int out_buf, int decode) {
+__device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>::U* __restrict__ keys,
+                                                typename Val<VB>::T* __restrict__ vals,
+                                                typename Key<KT>::U* __restrict__ tmpk,
+                                                typename Val<VB>::T* __restrict__ tmpv, int out_buf, int decode,
+                                                unsigned char* smem) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
   constexpr bool W = VB > 0;
   constexpr int CAP = THREADS * ITEMS;
   constexpr int PCAP = base_sort_pcap<sizeof(U)>(CAP);
   static_assert(PCAP % 4 == 0, "padded arrays must keep 16-byte alignment of the next array");
-  extern __shared__ __align__(16) unsigned char smem[];
   U* sk = reinterpret_cast<U*>(smem);
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + PCAP);
   V* sv = reinterpret_cast<V*>(si + (W ? PCAP : 0));
 
-  const Item it = items[blockIdx.x];
   const int m = (int)it.size;
   const int tid = threadIdx.x;
   // P: m rounded up to whole threads (at most ITEMS-1 padding elements); runs may be ragged
@@ -914,6 +915,16 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
     dstk[i] = decode ? Key<KT>::dec(c) : c;
     if (W) dstv[i] = sv[si[p]];
   }
+}
+
+template <int KT, int VB, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict__ keys,
+                 typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
+                 typename Val<VB>::T* __restrict__ tmpv, int out_buf, int decode) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Item it = items[blockIdx.x];
+  base_sort_block<KT, VB, THREADS, ITEMS>(it, keys, vals, tmpk, tmpv, out_buf, decode, smem);
 }
 
 template <int KS, int VB, int THREADS, int ITEMS>

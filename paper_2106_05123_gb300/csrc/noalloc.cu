@@ -41,7 +41,7 @@ using pdq::set_error;
 extern "C" int pdq_sort_keys_noalloc(void* d_keys, int64_t n, pdq_dtype key_dtype, void* cuda_stream,
                                      pdq_stats* stats) {
   if (stats) std::memset(stats, 0, sizeof(*stats));
-  const size_t need = pdq_workspace_bytes(n < 0 ? 0 : n, 1, key_dtype, 0);
+  const size_t need = pdq_workspace_bytes(n < 0 ? 0 : n, 0, key_dtype, 0);
   if (need == 0) return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
   if (n < 0) return set_error(PDQ_ERR_ARG, "n must be >= 0");
   if (n <= 1) return pdq_sort_keys(d_keys, n, key_dtype, nullptr, 0, cuda_stream, nullptr, stats);

@@ -16,6 +16,9 @@ struct Tuning {
   int base_cap;      // largest bucket for the shared-memory base sort (power of two)
   int bad_allowed;   // >0 forced start of the bad-split counter, -1 start at 0, 0 floor(log2 n)
   bool probe;        // run the sorted / reverse probe
+  int wait_us;       // bound of the persistent kernel's waits (0: 2 s)
+  int inject_wait;   // test hook: the persistent kernel first waits on a flag nobody sets
+  int seg_block;     // persistent kernel block size (256 or 512)
 };
 
 struct SortArgs {
@@ -38,11 +41,29 @@ struct Layout {
   int64_t base_cap[5];  // capacity of each class's list
 };
 
+// Arguments of the segmented sort.
+struct SegArgs {
+  void* keys;
+  void* vals;
+  const int64_t* offsets;
+  int64_t nseg;
+  int64_t n;
+  void* ws;
+  size_t ws_bytes;
+  cudaStream_t stream;
+  Tuning tune;
+  int num_sms;
+};
+
 int set_error(int code, const std::string& msg);
 
 template <int KT, int VB>
 int sort_impl(const SortArgs& a, pdq_stats* stats);
 template <int KT, int VB>
 size_t workspace_bytes_impl(int64_t n);
+template <int KT, int VB>
+int seg_sort_impl(const SegArgs& a, pdq_stats* stats);
+template <int KT, int VB>
+size_t seg_workspace_bytes_impl(int64_t n, int64_t nseg);
 
 }  // namespace pdq

@@ -179,6 +179,10 @@ class PlainSorter {
 
   pdq_stats stats_{};
 
+  // entry points used by the segmented path's host side
+  int configure_public() { return configure(); }
+  int fallback_public(const Item& it) { return fallback(it); }
+
  private:
   SortArgs a_;
   Layout L_;

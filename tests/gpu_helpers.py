@@ -33,7 +33,7 @@ def gpu_sort(keys: np.ndarray, vals: np.ndarray | None = None, tuning=None):
     dk = to_device(keys)
     n = keys.size
     vb = vals.dtype.itemsize if vals is not None else 0
-    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb)), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb, 0)), dtype=torch.uint8, device="cuda")
     if vals is None:
         st = pdq.pdq_sort_keys(dk, workspace=ws, tuning=tuning, key_dtype=code)
         torch.cuda.synchronize()
@@ -46,3 +46,29 @@ def gpu_sort(keys: np.ndarray, vals: np.ndarray | None = None, tuning=None):
 
 def bits(a: np.ndarray) -> np.ndarray:
     return a.view({4: np.uint32, 8: np.uint64}[a.dtype.itemsize])
+
+
+def gpu_sort_segmented(keys: np.ndarray, offsets: np.ndarray, vals: np.ndarray | None = None, tuning=None,
+                       raise_on_error=True):
+    """Segmented sort on the GPU; returns (keys, vals, stats, status)."""
+    code = CODE[keys.dtype]
+    dk = to_device(keys) if keys.size else torch.empty(16, dtype=CARRIER[keys.dtype.itemsize][1], device="cuda")
+    doff = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.int64)).cuda()
+    dv = to_device(vals) if vals is not None and vals.size else None
+    n = keys.size
+    nseg = max(0, offsets.size - 1)
+    vb = vals.dtype.itemsize if vals is not None else 0
+    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb, max(1, nseg))), dtype=torch.uint8,
+                     device="cuda")
+    import ctypes
+    st = pdq.Stats()
+    L = pdq.lib()
+    rc = L.pdq_sort_segmented(dk.data_ptr(), dv.data_ptr() if dv is not None else None, vb, doff.data_ptr(),
+                              nseg, n, code, ws.data_ptr(), ws.numel(),
+                              torch.cuda.current_stream().cuda_stream, pdq._tuning(tuning), ctypes.byref(st))
+    torch.cuda.synchronize()
+    if rc and raise_on_error:
+        raise pdq.PdqError(rc, L.pdq_last_error().decode())
+    kout = to_host(dk, keys.dtype)[:n]
+    vout = to_host(dv, vals.dtype)[:n] if dv is not None else None
+    return kout, vout, st.as_dict(), rc

@@ -27,7 +27,8 @@ def declared_functions():
 
 def test_header_declares_entry_points():
     names = declared_functions()
-    for must in ("pdq_sort_keys", "pdq_sort_pairs", "pdq_workspace_bytes", "pdq_last_error"):
+    for must in ("pdq_sort_keys", "pdq_sort_pairs", "pdq_sort_segmented", "pdq_workspace_bytes",
+                 "pdq_last_error"):
         assert must in names
 
 
@@ -43,6 +44,8 @@ def test_workspace_bytes_is_host_logic(L):
     pairs = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_I32, 4)
     wide = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_U64, 0)
     assert 0 < small < big < pairs and big < wide
+    seg = pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_I32, 0, num_segments=20000)
+    assert seg >= big                     # the segmented layout also covers the plain one
     assert big >= 4 * (1 << 20)          # at least the temp key buffer
     assert pdq.pdq_workspace_bytes(10, 7, 0) == 0       # unknown dtype
     assert pdq.pdq_workspace_bytes(10, pdq.PDQ_I32, 3) == 0
