@@ -50,12 +50,32 @@ WORKLOADS = {
                             np.uint64, np.uint32),
     "pairs_f32_normal_2p27": ("float32 N(0,1) keys with NaN/-0/inf + uint32 index, n=2^27", 1 << 27,
                               np.float32, np.uint32),
+    "segmented_i32_20k": ("20000 segments, lengths log-uniform in [1, 2^16], int32 uniform keys "
+                          "(batched persistent launch)", None, np.int32, None),
+    "segmented_i64_20k": ("20000 segments, lengths log-uniform in [1, 2^16], int64 uniform keys "
+                          "(batched persistent launch)", None, np.int64, None),
+    "learned_f32_mixture_2p28": ("float32 keys from an 8-component Gaussian/lognormal mixture, n=2^28, "
+                                 "learned-CDF path", 1 << 28, np.float32, None),
 }
+
+
+def kind_of(name: str) -> str:
+    return "segmented" if name.startswith("segmented") else ("learned" if name.startswith("learned") else "plain")
+
+
+def segment_layout():
+    offsets = workloads.segment_offsets(20000, workloads.config_seed(3), max_log2=16)
+    return offsets, int(offsets[-1])
 
 
 def make_inputs(name: str, rank: int):
     _, n, kdt, vdt = WORKLOADS[name]
     seed = workloads.config_seed(0) ^ rank
+    if name.startswith("segmented"):
+        _, total = segment_layout()
+        return [(workloads.uniform_bits(total, kdt, workloads.config_seed(3) ^ rank), None)]
+    if name.startswith("learned"):
+        return [(workloads.mixture_f32(n, workloads.config_seed(4) ^ rank)[0], None)]
     if name.startswith("uniform"):
         return [(workloads.uniform_bits(n, kdt, seed), None)]
     if name == "sweep_i32_2p24":
@@ -161,10 +181,7 @@ def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
             kk = k.copy()
             vv = v.copy() if v is not None else None
             t0 = time.perf_counter()
-            if vv is None:
-                oracle.pdqsort(kk)
-            else:
-                oracle.pdqsort_pairs(kk, vv)
+            oracle_sort_sample(name, kk, vv)
             t_total += time.perf_counter() - t0
             total_keys += k.size
         reps += 1
@@ -174,9 +191,27 @@ def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
                       f"{reps} repetition(s), {t_total:.1f} s of single-core CPU time"}
 
 
+def oracle_sort_sample(name: str, keys, vals) -> None:
+    """The CPU oracle on one bounded sample (segment by segment for the segmented workloads)."""
+    import oracle
+    if name.startswith("segmented"):
+        offsets, _ = segment_layout()
+        oracle.pdqsort_segmented(keys, offsets[:2001])
+    elif vals is None:
+        oracle.pdqsort(keys)
+    else:
+        oracle.pdqsort_pairs(keys, vals)
+
+
 def make_inputs_small(name: str):
     """Bounded samples of each workload for the CPU oracle (2^24 keys, or 2^22 for pairs)."""
     _, n, kdt, vdt = WORKLOADS[name]
+    if name.startswith("segmented"):  # the first 2000 segments' keys of the same layout
+        offsets, _ = segment_layout()
+        m = int(offsets[2000])
+        return [(workloads.uniform_bits(m, kdt, workloads.config_seed(3)), None)]
+    if name.startswith("learned"):
+        return [(workloads.mixture_f32(1 << 24, workloads.config_seed(4))[0], None)]
     m = min(n, 1 << 24) if vdt is None else min(n, 1 << 22)
     if name.startswith("uniform"):
         return [(workloads.uniform_bits(m, kdt, workloads.config_seed(0)), None)]
@@ -203,10 +238,7 @@ def run_reference(args, rank: int) -> None:
             kk = k.copy()
             vv = v.copy() if v is not None else None
             t0 = time.perf_counter()
-            if vv is None:
-                oracle.pdqsort(kk)
-            else:
-                oracle.pdqsort_pairs(kk, vv)
+            oracle_sort_sample(args.workload, kk, vv)
             t += time.perf_counter() - t0
             nk += k.size
         if step >= args.warmup:
@@ -230,7 +262,7 @@ def run_reference(args, rank: int) -> None:
 
 def dtype_name(name: str) -> str:
     _, _, kdt, vdt = WORKLOADS[name]
-    s = {np.int32: "int32", np.uint64: "uint64", np.float32: "f32"}[kdt]
+    s = {np.int32: "int32", np.int64: "int64", np.uint64: "uint64", np.float32: "f32"}[kdt]
     return s + ("+u32" if vdt is not None else "")
 
 
@@ -264,8 +296,12 @@ def bench_gpu(args, rank: int, world: int) -> None:
         dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
         dist = dist_mod
     desc, n, kdt, vdt = WORKLOADS[args.workload]
+    kind = kind_of(args.workload)
     host_inputs = make_inputs(args.workload, rank)
-    code = {np.int32: pdq.PDQ_I32, np.uint64: pdq.PDQ_U64, np.float32: pdq.PDQ_F32}[kdt]
+    if kind == "segmented":
+        offsets_h, n = segment_layout()
+        offsets_d = torch.from_numpy(offsets_h).cuda()
+    code = {np.int32: pdq.PDQ_I32, np.int64: pdq.PDQ_I64, np.uint64: pdq.PDQ_U64, np.float32: pdq.PDQ_F32}[kdt]
     kb = np.dtype(kdt).itemsize
     vb = np.dtype(vdt).itemsize if vdt is not None else 0
     carrier = {4: np.int32, 8: np.int64}
@@ -276,11 +312,21 @@ def bench_gpu(args, rank: int, world: int) -> None:
     pristine = [(dev(k), dev(v) if v is not None else None) for k, v in host_inputs]
     work_k = torch.empty_like(pristine[0][0])
     work_v = torch.empty_like(pristine[0][1]) if vb else None
-    ws = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, vb)), dtype=torch.uint8, device="cuda")
+    if kind == "segmented":
+        ws_bytes = pdq.pdq_workspace_bytes(n, code, vb, offsets_h.size - 1)
+    elif kind == "learned":
+        ws_bytes = pdq.pdq_workspace_bytes_learned(n)
+    else:
+        ws_bytes = pdq.pdq_workspace_bytes(n, code, vb)
+    ws = torch.empty(max(256, ws_bytes), dtype=torch.uint8, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     def one_sort(i):
+        if kind == "segmented":
+            return pdq.pdq_sort_segmented(work_k, offsets_d, workspace=ws, key_dtype=code)
+        if kind == "learned":
+            return pdq.pdq_sort_keys_learned(work_k, ws)
         if vb:
             return pdq.pdq_sort_pairs(work_k, work_v, ws, key_dtype=code)
         return pdq.pdq_sort_keys(work_k, ws, key_dtype=code)
@@ -305,7 +351,7 @@ def bench_gpu(args, rank: int, world: int) -> None:
         step()
     torch.cuda.synchronize()
     # correctness guard on the last warm-up result (properties that hold at any size)
-    if not vb and kdt == np.int32:
+    if not vb and kdt == np.int32 and kind == "plain":
         assert bool((work_k[1:] >= work_k[:-1]).all().item()), "output not sorted"
 
     sampler = ClockSampler(local)
@@ -371,14 +417,57 @@ def bench_gpu(args, rank: int, world: int) -> None:
                     hv.copy_(src_v[i])
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                pdq.pdq_sort_host(hk, work_k, ws, h_vals=hv, d_vals=work_v)  # returns after D2H
+                if kind == "plain":
+                    pdq.pdq_sort_host(hk, work_k, ws, h_vals=hv, d_vals=work_v)  # returns after D2H
+                else:
+                    work_k.copy_(hk, non_blocking=True)
+                    one_sort(i)
+                    hk.copy_(work_k, non_blocking=True)
+                    torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 if s > 0:
                     t_e2e += t1 - t0
         e2e = {"value": n * len(src_k) * e2e_steps * world / t_e2e / 1e9, "unit": "Gkeys/s",
                "h2d_bytes_per_step": n * (kb + vb) * len(src_k),
                "d2h_bytes_per_step": n * (kb + vb) * len(src_k),
-               "api": "pdq_sort_host", "steps": e2e_steps}
+               "api": "pdq_sort_host" if kind == "plain" else f"torch H2D + pdq_sort_{kind} + D2H",
+               "steps": e2e_steps}
+
+    # comparison arm on the same GB300 and data: the plain path (per segment, or on the whole array)
+    compare = None
+    if kind == "segmented":
+        work_k.copy_(pristine[0][0])
+        torch.cuda.synchronize()
+        ws_plain = torch.empty(max(256, pdq.pdq_workspace_bytes(int(np.diff(offsets_h).max()), code, 0)),
+                               dtype=torch.uint8, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s0, s1 in zip(offsets_h[:-1], offsets_h[1:]):
+            if s1 - s0 > 1:
+                pdq.pdq_sort_keys(work_k[s0:s1], ws_plain, key_dtype=code)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        compare = {"arm": "pdq_sort_keys looped over the 20000 segments (one step)",
+                   "value": n / (ms * 1e-3) / 1e9, "unit": "Gkeys/s", "ms_per_step": ms}
+    elif kind == "learned":
+        wsp = torch.empty(max(256, pdq.pdq_workspace_bytes(n, code, 0)), dtype=torch.uint8, device="cuda")
+        tms = []
+        for it in range(args.warmup + args.steps):
+            work_k.copy_(pristine[0][0])
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stp = pdq.pdq_sort_keys(work_k, wsp, key_dtype=code)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                tms.append(e0.elapsed_time(e1))
+        compare = {"arm": "plain sampled-splitter path (pdq_sort_keys) on the same keys",
+                   "value": n * len(tms) / (sum(tms) * 1e-3) / 1e9, "unit": "Gkeys/s",
+                   "ms_per_step": sum(tms) / len(tms), "stats": stp}
+    last_stats = step()
+    torch.cuda.synchronize()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -396,7 +485,9 @@ def bench_gpu(args, rank: int, world: int) -> None:
                                  "inputs larger than L2",
                            "parallelism": f"{world} independent sorts (one per GPU)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches, "wall_s_timed_region": t_wall}
+                "gpu_launches": launches, "wall_s_timed_region": t_wall, "stats": last_stats}
+        if compare is not None:
+            line["same_gpu_comparison"] = compare
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

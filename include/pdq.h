@@ -30,8 +30,10 @@
  *     256-byte aligned.  The library allocates no device memory of its own, except the
  *     segmented path's CUDA-graph cache (see pdq_sort_segmented).
  *   - n must be < 2^32.  n = 0 and n = 1 are no-ops.  value_bytes is 4 or 8.
- *   - d_keys and d_vals must be 16-byte aligned (tiles are staged by bulk copies); any
- *     allocation from cudaMalloc or PyTorch's allocator is.
+ *   - d_keys and d_vals need their natural alignment.  Internally tiles are staged by 16-byte
+ *     bulk copies from the 16-byte boundary at or below d_keys (up to 12 bytes before d_keys are
+ *     read, never written); with a payload, d_vals must sit at the same element offset from a
+ *     16-byte boundary as d_keys (true for any two arrays from cudaMalloc or PyTorch).
  *   - Return value: PDQ_OK or a negative pdq_status; pdq_last_error() gives a message (per
  *     host thread).  After PDQ_ERR_CUDA / PDQ_ERR_TIMEOUT / PDQ_ERR_INTERNAL the arrays hold
  *     an unspecified permutation of their input pairs.
@@ -118,6 +120,33 @@ int pdq_sort_pairs(void* d_keys, void* d_vals, int value_bytes, int64_t n, pdq_d
 int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_t* d_offsets,
                        int64_t num_segments, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
                        void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats);
+
+/* Learned-CDF proposal (float32 keys only, no payload).  A 1% sample of the keys is sorted and a
+ * monotone model F(x) = sum_j a_j sat(w_j (x - t_j)) (16 hidden units, a_j > 0, w_j > 0; a 2-layer
+ * MLP) is trained on it on the device by Adam on the squared error to the sample's empirical CDF.
+ * The model then maps every key straight to one of 4096 buckets (min(4095, trunc(4096 F(x))),
+ * NaNs by sign to the first or last bucket) in place of the first sampled-splitter level; every
+ * bucket larger than the base capacity is re-partitioned exactly by the splitter levels
+ * (stats.learned_overflow counts them).  The result is bit-identical to pdq_sort_keys.
+ *   d_ws: workspace of at least pdq_workspace_bytes_learned(n) bytes.  Other arguments as
+ *   pdq_sort_keys. */
+int pdq_sort_keys_learned(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                          void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats);
+size_t pdq_workspace_bytes_learned(int64_t n);
+
+/* Test probes of the learned model (parity of the hand-written forward/backward with a CPU
+ * reference).  theta = [alpha(16), omega(16), c(16)]: a = softmax(alpha), w = exp(omega),
+ * F(x) = sum_j a_j sat(w_j ((x - mu) / sigma - c_j)).
+ * pdq_learned_loss_grad: h_out[0..48) = sum over points of d/dtheta of 0.5 (F(x_i) - t_i)^2,
+ *   h_out[48] = sum of 0.5 (F(x_i) - t_i)^2; d_ws: >= 512 bytes of device scratch.
+ * pdq_learned_train: trains on the sorted sample d_xs[0..m) (targets (i + 0.5) / m) for `steps`
+ *   Adam steps of `batch` points; returns theta, [mu, sigma, first loss, last loss] and the
+ *   folded model's w, t, a (3 x 16 floats: h_j = sat(w_j (x - t_j))); d_ws: >= 1024 bytes of
+ *   device scratch. */
+int pdq_learned_loss_grad(const float* d_x, const float* d_targets, int64_t m, const float* h_theta,
+                          float mu, float sigma, float* h_out, void* d_ws, void* cuda_stream);
+int pdq_learned_train(const float* d_xs, int64_t m, int steps, int batch, float lr, void* d_ws,
+                      float* h_theta, float* h_norm_loss, float* h_wba, void* cuda_stream);
 
 /* Host-buffer convenience form of pdq_sort_keys / pdq_sort_pairs: copies h_keys (and h_vals
  * when value_bytes > 0) into the caller's device buffers d_keys / d_vals, sorts them there and

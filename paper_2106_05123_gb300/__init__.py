@@ -81,6 +81,15 @@ def lib() -> ctypes.CDLL:
             L.pdq_sort_segmented.argtypes = [vp, vp, i32, vp, i64, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
             L.pdq_sort_segmented.restype = i32
             L.pdq_sort_host.restype = i32
+            L.pdq_sort_keys_learned.argtypes = [vp, i64, i32, vp, sz, vp, P(Tuning), P(Stats)]
+            L.pdq_sort_keys_learned.restype = i32
+            L.pdq_workspace_bytes_learned.argtypes = [i64]
+            L.pdq_workspace_bytes_learned.restype = sz
+            fp = P(ctypes.c_float)
+            L.pdq_learned_loss_grad.argtypes = [vp, vp, i64, fp, ctypes.c_float, ctypes.c_float, fp, vp, vp]
+            L.pdq_learned_loss_grad.restype = i32
+            L.pdq_learned_train.argtypes = [vp, i64, i32, i32, ctypes.c_float, vp, fp, fp, fp, vp]
+            L.pdq_learned_train.restype = i32
             L.pdq_sort_keys_noalloc.argtypes = [vp, i64, i32, vp, P(Stats)]
             L.pdq_sort_keys_noalloc.restype = i32
             L.pdq_reverse.argtypes = [vp, i64, i32, vp]
@@ -219,6 +228,53 @@ def pdq_sort_host(h_keys: torch.Tensor, d_keys: torch.Tensor, workspace: torch.T
                                workspace.data_ptr(), workspace.numel(), _stream_ptr(stream),
                                _tuning(tuning), ctypes.byref(st)))
     return st.as_dict()
+
+
+def pdq_sort_keys_learned(keys: torch.Tensor, workspace: torch.Tensor | None = None, tuning=None,
+                          stream=None) -> dict:
+    """Learned-CDF sort of a float32 CUDA tensor in place (bit-identical to pdq_sort_keys)."""
+    _require_cuda(keys, "keys")
+    if keys.dtype != torch.float32:
+        raise PdqError(-2, "the learned path sorts float32 keys")
+    n = keys.numel()
+    ws = workspace if workspace is not None else torch.empty(
+        max(256, int(lib().pdq_workspace_bytes_learned(n))), dtype=torch.uint8, device=keys.device)
+    st = Stats()
+    _check(lib().pdq_sort_keys_learned(keys.data_ptr(), n, PDQ_F32, ws.data_ptr(), ws.numel(),
+                                       _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def pdq_workspace_bytes_learned(n: int) -> int:
+    return int(lib().pdq_workspace_bytes_learned(int(n)))
+
+
+def _fbuf(k):
+    return (ctypes.c_float * k)()
+
+
+def pdq_learned_loss_grad(x: torch.Tensor, targets: torch.Tensor, theta, mu: float, sigma: float,
+                          stream=None):
+    """Loss and gradient of the learned model's objective on the device (test probe)."""
+    th = _fbuf(48)
+    for i, v in enumerate(theta):
+        th[i] = float(v)
+    out = _fbuf(49)
+    ws = torch.empty(1024, dtype=torch.uint8, device=x.device)
+    _check(lib().pdq_learned_loss_grad(x.data_ptr(), targets.data_ptr(), x.numel(), th, float(mu),
+                                       float(sigma), out, ws.data_ptr(), _stream_ptr(stream)))
+    return float(out[48]), [float(out[i]) for i in range(48)]
+
+
+def pdq_learned_train(sorted_sample: torch.Tensor, steps: int = 64, batch: int = 16384, lr: float = 0.05,
+                      stream=None) -> dict:
+    """Train the learned model on a sorted float32 sample on the device (test probe)."""
+    th, nl, wba = _fbuf(48), _fbuf(4), _fbuf(48)
+    ws = torch.empty(4096, dtype=torch.uint8, device=sorted_sample.device)
+    _check(lib().pdq_learned_train(sorted_sample.data_ptr(), sorted_sample.numel(), int(steps), int(batch),
+                                   float(lr), ws.data_ptr(), th, nl, wba, _stream_ptr(stream)))
+    return {"theta": list(th), "mu": nl[0], "sigma": nl[1], "loss_first": nl[2], "loss_last": nl[3],
+            "w": list(wba[:16]), "t": list(wba[16:32]), "a": list(wba[32:48])}
 
 
 def pdq_sort_keys_noalloc(keys: torch.Tensor, stream=None, key_dtype: int | None = None) -> dict:

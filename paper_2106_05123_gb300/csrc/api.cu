@@ -206,9 +206,9 @@ static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int d
   if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8)
     return set_error(PDQ_ERR_ARG, "value_bytes must be 4 or 8");
   if (n <= 1) return PDQ_OK;
-  if (!keys || ((uintptr_t)keys % 16)) return set_error(PDQ_ERR_ARG, "keys pointer null or not 16-byte aligned");
-  if (value_bytes && (!vals || ((uintptr_t)vals % 16)))
-    return set_error(PDQ_ERR_ARG, "values pointer null or not 16-byte aligned");
+  if (!keys || ((uintptr_t)keys % kb)) return set_error(PDQ_ERR_ARG, "keys pointer null or misaligned");
+  if (value_bytes && (!vals || ((uintptr_t)vals % value_bytes)))
+    return set_error(PDQ_ERR_ARG, "values pointer null or misaligned");
   if (!ws || ((uintptr_t)ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
   SortArgs a;
   a.keys = keys;
@@ -303,9 +303,9 @@ int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_
     return set_error(PDQ_ERR_ARG, "value_bytes must be 0, 4 or 8");
   if (num_segments == 0 || n <= 1) return PDQ_OK;
   if (!d_offsets || ((uintptr_t)d_offsets % 8)) return set_error(PDQ_ERR_ARG, "offsets pointer null or misaligned");
-  if (!d_keys || ((uintptr_t)d_keys % 16)) return set_error(PDQ_ERR_ARG, "keys pointer null or not 16-byte aligned");
-  if (value_bytes && (!d_vals || ((uintptr_t)d_vals % 16)))
-    return set_error(PDQ_ERR_ARG, "values pointer null or not 16-byte aligned");
+  if (!d_keys || ((uintptr_t)d_keys % kb)) return set_error(PDQ_ERR_ARG, "keys pointer null or misaligned");
+  if (value_bytes && (!d_vals || ((uintptr_t)d_vals % value_bytes)))
+    return set_error(PDQ_ERR_ARG, "values pointer null or misaligned");
   if (!d_ws || ((uintptr_t)d_ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
   SegArgs a;
   a.keys = d_keys;
@@ -324,6 +324,29 @@ int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_
     case 4: return dispatch_seg<4>(key_dtype, a, stats);
     default: return dispatch_seg<8>(key_dtype, a, stats);
   }
+}
+
+int pdq_sort_keys_learned(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_ws, size_t ws_bytes,
+                          void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats) {
+  g_last_error.clear();
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (key_dtype != PDQ_F32) return set_error(PDQ_ERR_DTYPE, "the learned path sorts float32 keys");
+  if (n < 0 || n >= (int64_t(1) << 32)) return set_error(PDQ_ERR_ARG, "n must be in [0, 2^32)");
+  if (n <= 1) return PDQ_OK;
+  if (!d_keys || ((uintptr_t)d_keys % 4)) return set_error(PDQ_ERR_ARG, "keys pointer null or misaligned");
+  if (!d_ws || ((uintptr_t)d_ws % 256)) return set_error(PDQ_ERR_WORKSPACE, "workspace null or not 256-byte aligned");
+  if (ws_bytes < learned_workspace_bytes(n)) return set_error(PDQ_ERR_WORKSPACE, "workspace too small");
+  SortArgs a;
+  a.keys = d_keys;
+  a.vals = nullptr;
+  a.n = n;
+  a.ws = d_ws;
+  a.ws_bytes = ws_bytes;
+  a.stream = static_cast<cudaStream_t>(cuda_stream);
+  a.num_sms = num_sms();
+  int rc = make_tuning(tuning, &a.tune);
+  if (rc) return rc;
+  return learned_sort_f32(a, stats);
 }
 
 const char* pdq_last_error(void) { return g_last_error.c_str(); }

@@ -343,19 +343,63 @@ __device__ __forceinline__ void load_splitters(U* s_tree, U* s_spl, const U* tre
   }
 }
 
+// ================================================================== classifier policies
+// The distribution kernels are generic over how a code is mapped to its bin.
+//   SplitterCls: bins of sampled splitters (2B bins, odd bins hold keys equal to a splitter),
+//                prefilter table + Eytzinger tree, one splitter set per task.
+//   (the learned CDF model of the learned path is another policy, see learned.cuh)
+template <class U>
+struct SplitterCls {
+  static constexpr int kMaxBins = kBinsMax;
+  static constexpr bool kEqualBins = true;
+  struct Params {
+    const int32_t* task_logb;
+    const U* tree;
+    const U* spl;
+    const Pref<U>* pref;
+    const uint32_t* tab;
+  };
+  struct Shared {
+    U tree[kBMax], spl[kBMax];
+    uint32_t tab[kPrefEntries];
+    Pref<U> pf;
+    int logb;
+  };
+  // Fills the shared state of `task` (all threads); returns the task's number of bins.
+  __device__ static int setup(Shared& sh, const Params& p, int task) {
+    const int logb = p.task_logb[task];
+    const int B = 1 << logb;
+    load_splitters(sh.tree, sh.spl, p.tree + (size_t)task * kBMax, p.spl + (size_t)task * kBMax, B);
+    const Pref<U> pf = p.pref[task];
+    for (int k = threadIdx.x; k < pf.nent; k += blockDim.x) sh.tab[k] = p.tab[(size_t)task * kPrefEntries + k];
+    if (threadIdx.x == 0) {
+      sh.pf = pf;
+      sh.logb = logb;
+    }
+    return 2 * B;
+  }
+  // Calls f(classifier) with a classifier specialised for the task's depth.
+  template <class F>
+  __device__ static void with(const Shared& sh, const Params&, F&& f) {
+    with_logb(sh.logb, [&](auto LB) {
+      constexpr int L = decltype(LB)::value;
+      const Pref<U> pf = sh.pf;
+      f([&](U code) { return classify_fast<L>(code, sh.tree, sh.spl, sh.tab, pf); });
+    });
+  }
+};
+
 // ================================================================== count
 // One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE codes that stream
 // into STAGES shared buffers by bulk copy; elements of a window outside the chunk are masked
 // (only the first and last window have any), and the last window's sub-16-byte tail is
 // classified straight from global memory.  Every code is classified and counted in a shared
 // histogram, written to counts[chunk][bin] at the end.
-template <int KT, int THREADS, int TILE, int STAGES>
+template <int KT, class CLS, int THREADS, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
-             const int32_t* __restrict__ task_logb, const typename Key<KT>::U* __restrict__ keys,
-             const typename Key<KT>::U* __restrict__ tmp, const typename Key<KT>::U* __restrict__ tree_g,
-             const typename Key<KT>::U* __restrict__ spl_g, const Pref<typename Key<KT>::U>* __restrict__ pref_g,
-             const uint32_t* __restrict__ tab_g, uint32_t* __restrict__ counts, Counters* ctr) {
+             const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
+             typename CLS::Params cp, uint32_t* __restrict__ counts, int bin_stride, Counters* ctr) {
   using U = typename Key<KT>::U;
   constexpr int KS = sizeof(U);
   constexpr int VEC = 16 / KS;                // codes per 16-byte vector
@@ -364,18 +408,12 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   constexpr int BUF_BYTES = TILE * KS;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[STAGES];
-  __shared__ U s_tree[kBMax], s_spl[kBMax];
-  __shared__ uint32_t hist[kBinsMax];
-  __shared__ uint32_t s_tab[kPrefEntries];
+  __shared__ typename CLS::Shared cs;
+  __shared__ uint32_t hist[CLS::kMaxBins];
 
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
-  const int logb = task_logb[c.task];
-  const int B = 1 << logb;
-  const int nb = 2 * B;
-  load_splitters(s_tree, s_spl, tree_g + (size_t)c.task * kBMax, spl_g + (size_t)c.task * kBMax, B);
-  const Pref<U> pf = pref_g[c.task];
-  for (int k = threadIdx.x; k < pf.nent; k += THREADS) s_tab[k] = tab_g[(size_t)c.task * kPrefEntries + k];
+  const int nb = CLS::setup(cs, cp, c.task);
   for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&bars[i], 1);
@@ -401,11 +439,8 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
     for (int i = 0; i < STAGES && i < ntiles; ++i) issue(i);
   uint32_t parity = 0;
   bool failed = false;
-  with_logb(logb, [&](auto LB) {
-    constexpr int L = decltype(LB)::value;
-    auto count_one = [&](U x) {
-      atomicAdd(&hist[classify_fast<L>(enc ? x : Key<KT>::enc(x), s_tree, s_spl, s_tab, pf)], 1u);
-    };
+  CLS::with(cs, cp, [&](auto classify) {
+    auto count_one = [&](U x) { atomicAdd(&hist[classify(enc ? x : Key<KT>::enc(x))], 1u); };
     for (int tile = 0; tile < ntiles; ++tile) {
       const int stg = tile % STAGES;
       const int64_t ws = a0 + (int64_t)tile * TILE;
@@ -457,28 +492,28 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
     return;
   }
   __syncthreads();
-  uint32_t* out = counts + (size_t)blockIdx.x * kBinsMax;
+  uint32_t* out = counts + (size_t)blockIdx.x * bin_stride;
   for (int b = threadIdx.x; b < nb; b += THREADS) out[b] = hist[b];
 }
 
 // ================================================================== scan
 // One CTA per task: bin totals over the task's chunks, bin starts, and per-chunk write offsets
 // (relative to the task's first element), written over the counts.  Child (start, size) pairs
-// go to children[task][bin].
-template <int THREADS>
+// go to children[task * bin_stride + bin].
+template <int THREADS, int MAXBINS>
 __global__ void __launch_bounds__(THREADS)
-scan_kernel(const int32_t* __restrict__ task_logb, const int32_t* __restrict__ task_chunk0,
-            const int32_t* __restrict__ task_nchunks, uint32_t* __restrict__ counts,
+scan_kernel(const int32_t* __restrict__ task_nbins, const int32_t* __restrict__ task_chunk0,
+            const int32_t* __restrict__ task_nchunks, uint32_t* __restrict__ counts, int bin_stride,
             uint2* __restrict__ children) {
-  __shared__ uint32_t tot[kBinsMax];
-  __shared__ uint32_t start[kBinsMax];
+  __shared__ uint32_t tot[MAXBINS];
+  __shared__ uint32_t start[MAXBINS];
   __shared__ uint32_t wtmp[THREADS / 32 + 1];
   const int task = blockIdx.x;
-  const int nb = 2 << task_logb[task];
+  const int nb = task_nbins[task];
   const int c0 = task_chunk0[task], nc = task_nchunks[task];
   for (int b = threadIdx.x; b < nb; b += THREADS) {
     uint32_t s = 0;
-    for (int c = 0; c < nc; ++c) s += counts[(size_t)(c0 + c) * kBinsMax + b];
+    for (int c = 0; c < nc; ++c) s += counts[(size_t)(c0 + c) * bin_stride + b];
     tot[b] = s;
   }
   __syncthreads();
@@ -486,12 +521,12 @@ scan_kernel(const int32_t* __restrict__ task_logb, const int32_t* __restrict__ t
   for (int b = threadIdx.x; b < nb; b += THREADS) {
     uint32_t run = start[b];
     for (int c = 0; c < nc; ++c) {
-      uint32_t* p = counts + (size_t)(c0 + c) * kBinsMax + b;
+      uint32_t* p = counts + (size_t)(c0 + c) * bin_stride + b;
       const uint32_t v = *p;
       *p = run;
       run += v;
     }
-    children[(size_t)task * kBinsMax + b] = make_uint2(start[b], tot[b]);
+    children[(size_t)task * bin_stride + b] = make_uint2(start[b], tot[b]);
   }
 }
 
@@ -503,14 +538,12 @@ scan_kernel(const int32_t* __restrict__ task_logb, const int32_t* __restrict__ t
 // counts, stage the window in place grouped by bin (codes and values), then write each bin's
 // run to its next free slots in the destination buffer (coalesced within runs).  Keys of an
 // equality bin written to the key buffer are final and are decoded on the way out.
-template <int KT, int VB, int THREADS, int TILE>
+template <int KT, int VB, class CLS, int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS)
 scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
-               const int32_t* __restrict__ task_logb, typename Key<KT>::U* __restrict__ keys,
-               typename Val<VB>::T* __restrict__ vals, typename Key<KT>::U* __restrict__ tmpk,
-               typename Val<VB>::T* __restrict__ tmpv, const typename Key<KT>::U* __restrict__ tree_g,
-               const typename Key<KT>::U* __restrict__ spl_g, const Pref<typename Key<KT>::U>* __restrict__ pref_g,
-               const uint32_t* __restrict__ tab_g, const uint32_t* __restrict__ offsets, Counters* ctr) {
+               typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
+               typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv,
+               typename CLS::Params cp, const uint32_t* __restrict__ offsets, int bin_stride, Counters* ctr) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
   constexpr int KS = sizeof(U);
@@ -521,30 +554,26 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   constexpr int NV = TILE / VK / THREADS;           // code vectors per thread
   constexpr int ITEMS = NV * VK;
   static_assert(TILE % (VK * THREADS) == 0 && TILE % VA == 0, "window must split evenly");
+  static_assert(TILE <= 65536 && CLS::kMaxBins <= 65536, "rank and bin share one 32-bit word");
   constexpr int KBUF = TILE * KS;
   constexpr int VBUF = VB ? TILE * VS : 0;
+  constexpr int NBMAX = CLS::kMaxBins;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* stage_b = reinterpret_cast<uint16_t*>(smem + 2 * (KBUF + VBUF));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(smem + 2 * (KBUF + VBUF));  // per-window counts, then starts
+  uint32_t* cursor = hist + NBMAX;                                         // next write offset per bin
+  uint32_t* gbase = cursor + NBMAX;                                        // cursor - window start
+  uint16_t* stage_b = reinterpret_cast<uint16_t*>(gbase + NBMAX);
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ U s_tree[kBMax], s_spl[kBMax];
-  __shared__ uint32_t hist[kBinsMax];     // per-window counts, then window bin starts
-  __shared__ uint32_t cursor[kBinsMax];   // next write offset per bin (task-relative)
-  __shared__ uint32_t gbase[kBinsMax];    // cursor - window start, per bin
+  __shared__ typename CLS::Shared cs;
   __shared__ uint32_t wtmp[THREADS / 32 + 1];
-  __shared__ uint32_t s_tab[kPrefEntries];
 
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
-  const int logb = task_logb[c.task];
-  const int B = 1 << logb;
-  const int nb = 2 * B;
-  load_splitters(s_tree, s_spl, tree_g + (size_t)c.task * kBMax, spl_g + (size_t)c.task * kBMax, B);
+  const int nb = CLS::setup(cs, cp, c.task);
   for (int b = threadIdx.x; b < nb; b += THREADS) {
-    cursor[b] = offsets[(size_t)blockIdx.x * kBinsMax + b];
+    cursor[b] = offsets[(size_t)blockIdx.x * bin_stride + b];
     hist[b] = 0;
   }
-  const Pref<U> pf = pref_g[c.task];
-  for (int k = threadIdx.x; k < pf.nent; k += THREADS) s_tab[k] = tab_g[(size_t)c.task * kPrefEntries + k];
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -596,8 +625,7 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 
   uint32_t parity = 0;
   bool failed = false;
-  with_logb(logb, [&](auto LB) {
-    constexpr int L = decltype(LB)::value;
+  CLS::with(cs, cp, [&](auto classify) {
     for (int tile = 0; tile < ntiles; ++tile) {
       const int stg = tile & 1;
       const int64_t ws = a0 + (int64_t)tile * TILE;
@@ -633,7 +661,7 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
           code[e] = enc ? v[i] : Key<KT>::enc(v[i]);
           if (VB) val[e] = bv[k];
           if (valid) {
-            const int bin = classify_fast<L>(code[e], s_tree, s_spl, s_tab, pf);
+            const int bin = classify(code[e]);
             packed[e] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
           } else {
             packed[e] = 0xFFFFFFFFu;
@@ -663,7 +691,7 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         const int b = stage_b[i];
         const uint32_t o = gbase[b] + (uint32_t)i;
         const U k = bk[i];
-        dstk[o] = (dst_is_keys && (b & 1)) ? Key<KT>::dec(k) : k;  // equality bin: final, decode
+        dstk[o] = (CLS::kEqualBins && dst_is_keys && (b & 1)) ? Key<KT>::dec(k) : k;  // equality bin: final
         if (VB) dstv[o] = bv[i];
       }
       __syncthreads();  // buffer, stage_b and hist are free again
@@ -678,16 +706,17 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 }
 
 // ================================================================== bookkeeping (Sec. 4.1, Sec. 3)
-static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_logb,
-                                const uint2* __restrict__ children, int base_cap, Counters* ctr,
+static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_nbins,
+                                const uint2* __restrict__ children, int bin_stride, int equal_bins,
+                                int base_cap, Counters* ctr,
                                 Task* __restrict__ next, Item* __restrict__ base_items,
                                 Item* __restrict__ copy_items, Item* __restrict__ fb_items,
                                 ListCaps caps) {
   const int task = blockIdx.y;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb = 2 << task_logb[task];
+  const int nb = task_nbins[task];
   if (b >= nb) return;
-  const uint2 ch = children[(size_t)task * kBinsMax + b];
+  const uint2 ch = children[(size_t)task * bin_stride + b];
   if (ch.y == 0) return;
   const Task t = tasks[task];
   const int dst = t.buf == kBufKeys ? kBufTmp : kBufKeys;
@@ -701,7 +730,7 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
     if ((int64_t)k < cap) list[k] = it;
     else atomicAdd(&ctr->overflow, 1ull);
   };
-  if (b & 1) {  // equality bucket: every key equals the splitter, final (Sec. 3)
+  if (equal_bins && (b & 1)) {  // equality bucket: every key equals the splitter, final (Sec. 3)
     atomicAdd(&ctr->equal_buckets, 1ull);
     if (dst == kBufTmp) {
       push(copy_items, &ctr->n_copy, caps.copy_cap);

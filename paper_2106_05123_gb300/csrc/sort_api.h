@@ -39,6 +39,8 @@ struct Layout {
   int64_t task_cap, round_cap, chunk_cap, item_cap, fb_cap;
   int64_t base_off[5];  // first entry of each base-sort size class's list (in items)
   int64_t base_cap[5];  // capacity of each class's list
+  size_t learned_xs, learned_out;  // learned path only
+  int64_t learned_m;
 };
 
 // Arguments of the segmented sort.
@@ -63,6 +65,8 @@ template <int KT, int VB>
 size_t workspace_bytes_impl(int64_t n);
 template <int KT, int VB>
 int seg_sort_impl(const SegArgs& a, pdq_stats* stats);
+int learned_sort_f32(const SortArgs& a, pdq_stats* stats);
+size_t learned_workspace_bytes(int64_t n);
 template <int KT, int VB>
 size_t seg_workspace_bytes_impl(int64_t n, int64_t nseg);
 

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "learned.cuh"
 #include "sort_api.h"
 
 namespace pdq {
@@ -19,7 +20,11 @@ inline int64_t chunk_min_for(int64_t n) {
   return c > 8192 ? c : 8192;
 }
 
-inline Layout make_layout(int64_t n, int ks, int vb) {
+constexpr int kTrainSteps = 48;       // Adam steps of the learned model
+constexpr int kTrainBatch = 8192;     // points per step, drawn from the 1% sample
+constexpr float kTrainLr = 0.05f;
+
+inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int64_t cmin = kBaseCapMin;
@@ -42,12 +47,13 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
     off = align_up(off + bytes, 256);
     return o;
   };
-  L.tmpk = take((size_t)n * ks);
-  L.tmpv = take((size_t)n * vb);
+  // temp buffers index like the (aligned-down) key buffer: up to 16 bytes of shift
+  L.tmpk = take((size_t)(n + 16 / ks) * ks);
+  L.tmpv = take((size_t)(n + (vb ? 16 / vb : 0)) * vb);
   L.ctr = take(sizeof(Counters));
   L.tasks_cur = take((size_t)L.round_cap * sizeof(Task));
   L.tasks_next = take((size_t)L.task_cap * sizeof(Task));
-  L.task_meta = take((size_t)L.round_cap * 3 * sizeof(int32_t));
+  L.task_meta = take((size_t)L.round_cap * 4 * sizeof(int32_t));
   L.chunks = take((size_t)L.chunk_cap * sizeof(Chunk));
   L.counts = take((size_t)L.chunk_cap * kBinsMax * sizeof(uint32_t));
   L.tree = take((size_t)L.round_cap * kBMax * ks);
@@ -58,6 +64,11 @@ inline Layout make_layout(int64_t n, int ks, int vb) {
   L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
+  if (learned) {  // 1% training sample and the trained model (learned path, float32 keys)
+    L.learned_m = std::min<int64_t>(n, std::max<int64_t>(4096, n / 100));
+    L.learned_xs = take((size_t)L.learned_m * sizeof(float));
+    L.learned_out = take(sizeof(TrainOut));
+  }
   L.total = off;
   return L;
 }
@@ -69,8 +80,8 @@ struct Shape {
   // buffered, staged in place; plus 2 bytes of bin id per element
   static constexpr int kScatterThreads = 512;
   static constexpr int kScatterTile = (KS + VB) <= 4 ? 8192 : ((KS + VB) <= 8 ? 4096 : 2048);
-  static constexpr size_t kScatterSmem =
-      2 * ((size_t)kScatterTile * KS + (size_t)kScatterTile * VB) + (size_t)kScatterTile * 2;
+  static constexpr size_t kScatterSmem = 2 * ((size_t)kScatterTile * KS + (size_t)kScatterTile * VB) +
+                                         3 * (size_t)kBinsMax * 4 + (size_t)kScatterTile * 2;
   // count: 512 threads, four 16 KiB tiles in flight
   static constexpr int kCountThreads = 512;
   static constexpr int kCountTile = 16384 / KS;
@@ -111,12 +122,18 @@ class PlainSorter {
   using S = Shape<KS, VB>;
 
  public:
-  PlainSorter(const SortArgs& a) : a_(a) {
+  explicit PlainSorter(const SortArgs& a, bool learned = false) : a_(a) {
     cap_ = std::min(a.tune.base_cap, S::kMaxCap);
-    L_ = make_layout(a.n, KS, VB);
+    L_ = make_layout(a.n, KS, VB, learned);
     char* ws = static_cast<char*>(a.ws);
-    keys_ = static_cast<U*>(a.keys);
-    vals_ = static_cast<V*>(a.vals);
+    // The tile kernels need 16-byte-aligned buffers: a key array that starts off a 16-byte
+    // boundary is addressed from the boundary below it, and every index is shifted by off_
+    // elements (reads of those leading elements are masked; nothing outside [off_, off_ + n) is
+    // written).  Values must share the same shift.
+    off_ = (int64_t)(((uintptr_t)a.keys % 16) / KS);
+    keys_ = static_cast<U*>(a.keys) - off_;
+    vals_ = VB ? static_cast<V*>(a.vals) - off_ : static_cast<V*>(a.vals);
+    vals_misaligned_ = VB && ((uintptr_t)vals_ % 16) != 0;
     tmpk_ = reinterpret_cast<U*>(ws + L_.tmpk);
     tmpv_ = reinterpret_cast<V*>(ws + L_.tmpv);
     ctr_ = reinterpret_cast<Counters*>(ws + L_.ctr);
@@ -137,45 +154,35 @@ class PlainSorter {
   }
 
   int run() {
-    if (a_.ws_bytes < L_.total) return set_error(PDQ_ERR_WORKSPACE, "workspace too small");
-    int rc = configure();
-    if (rc) return rc;
-    const int64_t n = a_.n;
-    if (n <= 1) return PDQ_OK;
-    const int cap = cap_;
-    if (n <= cap) {
-      Item it{0, (uint32_t)n, kBufKeys, 0};
-      const int cls = base_class_of(n);
-      PDQ_CUDA(cudaMemcpyAsync(base_items_ + L_.base_off[cls], &it, sizeof(it),
-                               cudaMemcpyHostToDevice, st_));
-      return base_sort(cls, 1, kBufKeys, 1, n);
-    }
-    if (a_.tune.probe) {
-      bool done = false;
-      rc = probe(&done);
-      if (rc || done) return rc;
-    }
-    const int bad0 = a_.tune.bad_allowed > 0 ? a_.tune.bad_allowed
-                                              : (a_.tune.bad_allowed < 0 ? 0 : ilog2_floor((uint64_t)n));
-    if (bad0 == 0) {
-      Item it{0, (uint32_t)n, kBufKeys, 0};
-      ++stats_.fallback_buckets;
-      return fallback(it);
-    }
+    bool done = false;
+    int bad0 = 0;
+    int rc = prologue(&done, &bad0);
+    if (rc || done) return rc;
     std::vector<Task> cur(1);
-    cur[0] = Task{0, n, kBufKeys, 0, bad0, 0};
-    while (!cur.empty()) {
-      std::vector<Task> nxt;
-      ++stats_.passes;
-      for (size_t r0 = 0; r0 < cur.size(); r0 += (size_t)L_.round_cap) {
-        const size_t r1 = std::min(cur.size(), r0 + (size_t)L_.round_cap);
-        rc = level_round(cur.data() + r0, (int)(r1 - r0), &nxt);
-        if (rc) return rc;
-      }
-      cur.swap(nxt);
-    }
-    return PDQ_OK;
+    cur[0] = Task{off_, a_.n, kBufKeys, 0, bad0, 0};
+    return level_loop(std::move(cur));
   }
+
+  // Learned path (float32 keys): a trained monotone CDF model cuts the array into 4096
+  // buckets in place of the first sampled-splitter level; buckets above the base capacity
+  // continue through the exact splitter levels (the overflow repair).
+  int run_learned() {
+    bool done = false;
+    int bad0 = 0;
+    int rc = prologue(&done, &bad0);
+    if (rc || done) return rc;
+    std::vector<Task> nxt;
+    if constexpr (KT == PDQ_F32 && VB == 0) {
+      ++stats_.passes;
+      rc = learned_round(bad0, &nxt);
+      if (rc) return rc;
+    } else {
+      return set_error(PDQ_ERR_DTYPE, "the learned path sorts float32 keys without values");
+    }
+    return level_loop(std::move(nxt));
+  }
+
+  TrainOut train_out_{};
 
   pdq_stats stats_{};
 
@@ -187,6 +194,8 @@ class PlainSorter {
   SortArgs a_;
   Layout L_;
   int cap_;  // base capacity for this key/value width
+  int64_t off_ = 0;  // element shift of the key buffer from its 16-byte boundary
+  bool vals_misaligned_ = false;
   U *keys_, *tmpk_, *tree_, *spl_;
   V *vals_, *tmpv_;
   Counters* ctr_;
@@ -200,6 +209,161 @@ class PlainSorter {
   Item *base_items_, *copy_items_, *fb_items_;
   cudaStream_t st_;
 
+  // Checks, the single-bucket case, the sorted / reverse probe and the zero-budget fallback.
+  // Sets *done when nothing more is needed, else the root's bad-split budget.
+  int prologue(bool* done, int* bad0_out) {
+    *done = true;
+    if (a_.ws_bytes < L_.total) return set_error(PDQ_ERR_WORKSPACE, "workspace too small");
+    if (vals_misaligned_)
+      return set_error(PDQ_ERR_ARG, "keys and values must sit at the same offset from a 16-byte boundary");
+    int rc = configure();
+    if (rc) return rc;
+    const int64_t n = a_.n;
+    if (n <= 1) return PDQ_OK;
+    const int cap = cap_;
+    if (n <= cap) {
+      Item it{off_, (uint32_t)n, kBufKeys, 0};
+      const int cls = base_class_of(n);
+      PDQ_CUDA(cudaMemcpyAsync(base_items_ + L_.base_off[cls], &it, sizeof(it),
+                               cudaMemcpyHostToDevice, st_));
+      return base_sort(cls, 1, kBufKeys, 1, n);
+    }
+    if (a_.tune.probe) {
+      bool sorted = false;
+      rc = probe(&sorted);
+      if (rc || sorted) return rc;
+    }
+    const int bad0 = a_.tune.bad_allowed > 0 ? a_.tune.bad_allowed
+                                              : (a_.tune.bad_allowed < 0 ? 0 : ilog2_floor((uint64_t)n));
+    if (bad0 == 0) {
+      Item it{off_, (uint32_t)n, kBufKeys, 0};
+      ++stats_.fallback_buckets;
+      return fallback(it);
+    }
+    *done = false;
+    *bad0_out = bad0;
+    return PDQ_OK;
+  }
+
+  int level_loop(std::vector<Task> cur) {
+    while (!cur.empty()) {
+      std::vector<Task> nxt;
+      ++stats_.passes;
+      for (size_t r0 = 0; r0 < cur.size(); r0 += (size_t)L_.round_cap) {
+        const size_t r1 = std::min(cur.size(), r0 + (size_t)L_.round_cap);
+        const int rc = level_round(cur.data() + r0, (int)(r1 - r0), &nxt);
+        if (rc) return rc;
+      }
+      cur.swap(nxt);
+    }
+    return PDQ_OK;
+  }
+
+  // The learned level over the whole array (one task).
+  int learned_round(int bad0, std::vector<Task>* nxt) {
+    if constexpr (KT == PDQ_F32 && VB == 0) {
+      constexpr int kTrainThreads = 512;
+      constexpr int kLTile = 4096;
+      constexpr size_t kLScatterSmem = 2 * (size_t)kLTile * 4 + 3 * (size_t)kLearnedBuckets * 4 + (size_t)kLTile * 2;
+      static bool configured = false;
+      if (!configured) {
+        PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, ModelCls, S::kCountThreads, S::kCountTile, S::kCountStages>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kCountSmem));
+        PDQ_CUDA(cudaFuncSetAttribute(scatter_kernel<KT, 0, ModelCls, 512, kLTile>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLScatterSmem));
+        configured = true;
+      }
+      const int64_t n = a_.n, m = L_.learned_m;
+      char* ws = static_cast<char*>(a_.ws);
+      float* xs = reinterpret_cast<float*>(ws + L_.learned_xs);
+      TrainOut* tout = reinterpret_cast<TrainOut*>(ws + L_.learned_out);
+      const uint64_t seed = mix64((uint64_t)n ^ 0x5EEDull);
+      {  // 1% sample at hashed positions
+        LaunchScope ls("learned_gather", st_, (double)m * 8);
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, a_.num_sms * 8));
+        learned_gather_kernel<<<blocks, 256, 0, st_>>>(reinterpret_cast<const float*>(keys_ + off_), n, xs, m, seed);
+      }
+      PDQ_LAUNCHED("learned_gather");
+      {  // sort the sample with the plain path (its workspace is the part before the sample)
+        SortArgs sa = a_;
+        sa.keys = xs;
+        sa.vals = nullptr;
+        sa.n = m;
+        sa.ws_bytes = L_.learned_xs;
+        PlainSorter<PDQ_F32, 0> sub(sa);
+        const int rc = sub.run();
+        if (rc) return rc;
+      }
+      {
+        LaunchScope ls("learned_train", st_, 0.0);
+        learned_train_kernel<kTrainThreads><<<1, kTrainThreads, 0, st_>>>(xs, m, kTrainSteps, kTrainBatch,
+                                                                         kTrainLr, seed ^ 0x7A11ull, tout);
+      }
+      PDQ_LAUNCHED("learned_train");
+      PDQ_CUDA(cudaMemcpyAsync(&train_out_, tout, sizeof(TrainOut), cudaMemcpyDeviceToHost, st_));
+      PDQ_CUDA(cudaStreamSynchronize(st_));
+      const LearnedModel model = train_out_.model;
+      // one task in about one large chunk per SM (keeps the 4096-bin scan short); chunks x 4096
+      // bins must fit the count array
+      int64_t ch = std::max<int64_t>(chunk_min_for(n), (n + a_.num_sms - 1) / a_.num_sms);
+      const int64_t max_chunks = std::max<int64_t>(1, L_.chunk_cap * kBinsMax / kLearnedBuckets);
+      ch = std::max<int64_t>(ch, (n + max_chunks - 1) / max_chunks);
+      std::vector<Chunk> chunks;
+      for (int64_t o = 0; o < n; o += ch) chunks.push_back(Chunk{off_ + o, (int32_t)std::min<int64_t>(ch, n - o), 0});
+      const int nchunks = (int)chunks.size();
+      const Task root{off_, n, kBufKeys, 0, bad0, 0};
+      const int32_t meta[4] = {0, 0, nchunks, kLearnedBuckets};  // logb (unused), chunk0, nchunks, nbins
+      PDQ_CUDA(cudaMemcpyAsync(tasks_, &root, sizeof(Task), cudaMemcpyHostToDevice, st_));
+      PDQ_CUDA(cudaMemcpyAsync(meta_, meta, sizeof(meta), cudaMemcpyHostToDevice, st_));
+      PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
+      PDQ_CUDA(cudaMemsetAsync(ctr_, 0, offsetof(Counters, probe), st_));
+      const int32_t* d_c0 = meta_ + 1;
+      const int32_t* d_nc = meta_ + 2;
+      const int32_t* d_nb = meta_ + 3;
+      {
+        LaunchScope ls("learned_count", st_, (double)n * KS);
+        count_kernel<KT, ModelCls, S::kCountThreads, S::kCountTile, S::kCountStages>
+            <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, model, counts_,
+                                                                kLearnedBuckets, ctr_);
+      }
+      PDQ_LAUNCHED("learned_count");
+      {
+        LaunchScope ls("learned_scan", st_, 0.0);
+        scan_kernel<1024, kLearnedBuckets><<<1, 1024, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kLearnedBuckets, children_);
+      }
+      PDQ_LAUNCHED("learned_scan");
+      {
+        LaunchScope ls("learned_scatter", st_, 2.0 * (double)n * KS);
+        scatter_kernel<KT, 0, ModelCls, 512, kLTile><<<nchunks, 512, kLScatterSmem, st_>>>(
+            chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, ctr_);
+      }
+      PDQ_LAUNCHED("learned_scatter");
+      {
+        LaunchScope ls("bookkeep", st_, 0.0);
+        ListCaps caps;
+        for (int c = 0; c < kBaseClasses; ++c) {
+          caps.base_off[c] = L_.base_off[c];
+          caps.base_cap[c] = L_.base_cap[c];
+        }
+        caps.task_cap = L_.task_cap;
+        caps.copy_cap = L_.item_cap;
+        caps.fb_cap = L_.fb_cap;
+        dim3 grid((unsigned)(kLearnedBuckets + 255) / 256, 1);
+        bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_nb, children_, kLearnedBuckets, 0, cap_, ctr_, next_,
+                                                 base_items_, copy_items_, fb_items_, caps);
+      }
+      PDQ_LAUNCHED("bookkeep");
+      Counters h;
+      const int rc = finish_round(nxt, &h);
+      stats_.learned_overflow = (int64_t)(h.n_next + h.n_fallback);
+      return rc;
+    } else {
+      (void)bad0;
+      (void)nxt;
+      return set_error(PDQ_ERR_DTYPE, "the learned path sorts float32 keys without values");
+    }
+  }
+
   template <int CLS>
   int configure_base() {
     constexpr int T = S::base_threads(CLS);
@@ -212,9 +376,9 @@ class PlainSorter {
   int configure() {
     static bool done = false;  // per template instantiation
     if (done) return PDQ_OK;
-    PDQ_CUDA(cudaFuncSetAttribute(scatter_kernel<KT, VB, S::kScatterThreads, S::kScatterTile>,
+    PDQ_CUDA(cudaFuncSetAttribute(scatter_kernel<KT, VB, SplitterCls<U>, S::kScatterThreads, S::kScatterTile>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kScatterSmem));
-    PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, S::kCountThreads, S::kCountTile, S::kCountStages>,
+    PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kCountSmem));
     int rc = configure_base<0>();
     if (!rc) rc = configure_base<1>();
@@ -242,7 +406,7 @@ class PlainSorter {
       if (blocks < 1) blocks = 1;
       {
         LaunchScope ls("probe", st_, (double)m * KS);
-        probe_kernel<KT><<<blocks, threads, 0, st_>>>(keys_, n, stride, m, ctr_->probe);
+        probe_kernel<KT><<<blocks, threads, 0, st_>>>(keys_ + off_, n, stride, m, ctr_->probe);
       }
       PDQ_LAUNCHED("probe");
       PDQ_CUDA(cudaMemcpyAsync(h, ctr_->probe, sizeof(h), cudaMemcpyDeviceToHost, st_));
@@ -270,8 +434,8 @@ class PlainSorter {
                                                                        (int64_t)a_.num_sms * 16));
       {
         LaunchScope ls("reverse", st_, 2.0 * n * (KS + VB));
-        reverse_kernel<U><<<blocks, threads, 0, st_>>>(keys_, n);
-        if (VB) reverse_kernel<V><<<blocks, threads, 0, st_>>>(vals_, n);
+        reverse_kernel<U><<<blocks, threads, 0, st_>>>(keys_ + off_, n);
+        if (VB) reverse_kernel<V><<<blocks, threads, 0, st_>>>(vals_ + off_, n);
       }
       PDQ_LAUNCHED("reverse");
       return PDQ_OK;
@@ -281,6 +445,16 @@ class PlainSorter {
 
   // Buckets per level: enough that the expected bucket is a quarter of the base capacity (so
   // that, with sampling noise, almost every bucket fits the base sort after this level).
+  typename SplitterCls<U>::Params cls_params(const int32_t* d_logb) const {
+    typename SplitterCls<U>::Params p;
+    p.task_logb = d_logb;
+    p.tree = tree_;
+    p.spl = spl_;
+    p.pref = pref_;
+    p.tab = tab_;
+    return p;
+  }
+
   int choose_logb(int64_t size) const {
     const int64_t quarter = std::max<int64_t>(1, cap_ / 4);
     const int64_t want = (size + quarter - 1) / quarter;
@@ -296,7 +470,7 @@ class PlainSorter {
     int64_t total = 0;
     for (int i = 0; i < nt; ++i) total += tasks[i].size;
     int64_t ch = std::max<int64_t>(chunk_min_for(n), (total + a_.num_sms * 4 - 1) / (a_.num_sms * 4));
-    std::vector<int32_t> meta(3 * (size_t)nt);
+    std::vector<int32_t> meta(4 * (size_t)nt);
     std::vector<Chunk> chunks;
     chunks.reserve((size_t)(total / ch + nt + 1));
     int max_logb = 1;
@@ -309,12 +483,14 @@ class PlainSorter {
       for (int64_t o = 0; o < tasks[i].size; o += ch, ++nc)
         chunks.push_back(Chunk{tasks[i].begin + o, (int32_t)std::min<int64_t>(ch, tasks[i].size - o), i});
       meta[2 * nt + i] = nc;
+      meta[3 * nt + i] = 2 << lb;
     }
     const int nchunks = (int)chunks.size();
     if (nchunks > L_.chunk_cap) return set_error(PDQ_ERR_INTERNAL, "chunk capacity exceeded");
     int32_t* d_logb = meta_;
     int32_t* d_c0 = meta_ + nt;
     int32_t* d_nc = meta_ + 2 * nt;
+    int32_t* d_nb = meta_ + 3 * nt;
     PDQ_CUDA(cudaMemcpyAsync(tasks_, tasks, sizeof(Task) * nt, cudaMemcpyHostToDevice, st_));
     PDQ_CUDA(cudaMemcpyAsync(meta_, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice, st_));
     PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
@@ -329,21 +505,21 @@ class PlainSorter {
     PDQ_LAUNCHED("sample");
     {
       LaunchScope ls("count", st_, (double)total * KS);
-      count_kernel<KT, S::kCountThreads, S::kCountTile, S::kCountStages>
-          <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, d_logb, keys_, tmpk_, tree_,
-                                                              spl_, pref_, tab_, counts_, ctr_);
+      count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>
+          <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, cls_params(d_logb),
+                                                              counts_, kBinsMax, ctr_);
     }
     PDQ_LAUNCHED("count");
     {
       LaunchScope ls("scan", st_, 0.0);
-      scan_kernel<256><<<nt, 256, 0, st_>>>(d_logb, d_c0, d_nc, counts_, children_);
+      scan_kernel<256, kBinsMax><<<nt, 256, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kBinsMax, children_);
     }
     PDQ_LAUNCHED("scan");
     {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
-      scatter_kernel<KT, VB, S::kScatterThreads, S::kScatterTile>
+      scatter_kernel<KT, VB, SplitterCls<U>, S::kScatterThreads, S::kScatterTile>
           <<<nchunks, S::kScatterThreads, S::kScatterSmem, st_>>>(
-              chunks_, tasks_, d_logb, keys_, vals_, tmpk_, tmpv_, tree_, spl_, pref_, tab_, counts_, ctr_);
+              chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, ctr_);
     }
     PDQ_LAUNCHED("scatter");
     {
@@ -357,11 +533,18 @@ class PlainSorter {
       caps.task_cap = L_.task_cap;
       caps.copy_cap = L_.item_cap;
       caps.fb_cap = L_.fb_cap;
-      bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_logb, children_, cap_, ctr_, next_,
+      bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_nb, children_, kBinsMax, 1, cap_, ctr_, next_,
                                                base_items_, copy_items_, fb_items_, caps);
     }
     PDQ_LAUNCHED("bookkeep");
     Counters h;
+    return finish_round(nxt, &h);
+  }
+
+  // After a round's bookkeeping: read the counters, sort finished buckets, copy final buckets
+  // home, run fallbacks, and collect the next level's tasks.
+  int finish_round(std::vector<Task>* nxt, Counters* hout) {
+    Counters& h = *hout;
     PDQ_CUDA(cudaMemcpyAsync(&h, ctr_, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
     PDQ_CUDA(cudaStreamSynchronize(st_));
     if (h.timeout) return set_error(PDQ_ERR_TIMEOUT, "a tile copy did not complete within its bounded wait");

@@ -1,0 +1,59 @@
+"""Pins for the double-precision reference of the learned-CDF model (CPU only): the analytic
+gradient matches central finite differences; at the initial point every ramp spans one
+sixteenth of the sample, so F interpolates the sample's empirical CDF at the 17 quantile knots;
+the model is monotone; buckets of a monotone model are ordered."""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import learned as L
+
+
+def _setup(seed):
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.normal(0, 3, 4000))
+    mu, sigma = float(x[x.size // 2]), float(x[-1] - x[0])
+    theta = L.init_theta(x, mu, sigma) + rng.normal(0, 0.05, 48)
+    t = (np.arange(x.size) + 0.5) / x.size
+    return x, t, mu, sigma, theta
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_gradient_matches_finite_differences(seed):
+    x, t, mu, sigma, theta = _setup(seed)
+    _, g = L.loss_grad(theta, x, t, mu, sigma)
+    num = np.zeros_like(theta)
+    h = 1e-6
+    for k in range(theta.size):
+        d = np.zeros_like(theta)
+        d[k] = h
+        num[k] = (L.loss(theta + d, x, t, mu, sigma) - L.loss(theta - d, x, t, mu, sigma)) / (2 * h)
+    # clamp kinks make isolated points non-differentiable; compare in norm
+    assert np.linalg.norm(g - num) <= 1e-4 * max(1.0, np.linalg.norm(num))
+
+
+def test_initial_point_interpolates_quantiles():
+    x = np.sort(workloads.mixture_f32(20000, 3)[0].astype(np.float64))
+    mu, sigma = float(x[x.size // 2]), float(x[-1] - x[0])
+    theta = L.init_theta(x, mu, sigma)
+    n = x.size
+    for j in range(17):
+        q = x[min(n - 1, (n * j) // 16)] if j < 16 else x[-1]
+        F = L.forward(theta, np.array([q]), mu, sigma)[0][0]
+        assert abs(F - j / 16) < 1.0 / 16 + 1e-9  # within one ramp of the knot's CDF value
+    F0 = L.forward(theta, np.array([x[0]]), mu, sigma)[0][0]
+    F1 = L.forward(theta, np.array([x[-1]]), mu, sigma)[0][0]
+    assert F0 < 0.01 and F1 > 0.99
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_model_is_monotone_and_buckets_ordered(seed):
+    x, t, mu, sigma, theta = _setup(seed)
+    grid = np.linspace(x[0] - 10, x[-1] + 10, 20001)
+    F = L.forward(theta, grid, mu, sigma)[0]
+    assert np.all(np.diff(F) >= 0)
+    b = L.buckets(theta, grid, mu, sigma)
+    assert np.all(np.diff(b) >= 0) and b.min() >= 0 and b.max() <= 4095
+    nan_b = L.buckets(theta, np.array([-np.nan, np.nan, np.copysign(np.nan, -1.0)]), mu, sigma)
+    assert nan_b[1] == 4095 and nan_b[2] == 0
