@@ -199,8 +199,25 @@ __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, co
 // b_lo = #splitters < first code and b_hi = #splitters <= last code of the slice, so every
 // code of the slice has rank (#splitters < code) in [b_lo, b_hi].  Codes outside [lo, hi] are
 // clamped into the first or last slice, whose bounds still hold for them.
-constexpr int kPrefBits = 11;
-constexpr int kPrefEntries = 1 << kPrefBits;
+// When b_hi <= b_lo + 1 the entry's candidate s0 = spl[b_lo] settles both the rank
+// (b_lo + [s0 < code]) and the equality test (code == s0): splitter b_lo + 1, if any, lies above
+// the slice and so cannot equal a code in it.
+constexpr int kPrefBitsMax = 11;
+constexpr int kPrefEntriesMax = 1 << kPrefBitsMax;
+
+// Table size per key width: 2048 entries of 8 bytes (4-byte codes) or 1024 of 16 bytes.
+template <class U>
+__host__ __device__ constexpr int pref_bits() { return sizeof(U) == 4 ? 11 : 10; }
+template <class U>
+__host__ __device__ constexpr int pref_entries() { return 1 << pref_bits<U>(); }
+
+// One slice: rank bounds (b_lo | b_hi << 16) and the slice's candidate splitter
+// s0 = spl[min(b_lo, B - 2)], the only splitter a code of a one-candidate slice is compared with.
+template <class U>
+struct alignas(2 * sizeof(U)) PrefEnt {
+  U range;
+  U s0;
+};
 
 template <class U>
 struct Pref {
@@ -213,24 +230,66 @@ struct Pref {
 // one predicated comparison (branch-free); a wider slice falls back to the Eytzinger descent.
 template <int LOGB, class U>
 __device__ __forceinline__ int classify_fast(U code, const U* __restrict__ tree, const U* __restrict__ spl,
-                                             const uint32_t* __restrict__ tab, const Pref<U>& pf) {
+                                             const PrefEnt<U>* __restrict__ tab, const Pref<U>& pf) {
   constexpr int B = 1 << LOGB;
   const U y = code < pf.lo ? pf.lo : (code > pf.hi ? pf.hi : code);
-  const uint32_t e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
-  const int blo = (int)(e & 0xFFFFu), bhi = (int)(e >> 16);
-  int b;
+  const PrefEnt<U> e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
+  const int blo = (int)(e.range & 0xFFFFu), bhi = (int)((e.range >> 16) & 0xFFFFu);
   if (bhi - blo <= 1) {
-    const int k = blo < B - 2 ? blo : B - 2;  // == blo whenever blo < bhi
-    b = blo + ((blo < bhi && spl[k] < code) ? 1 : 0);
-  } else {
-    int j = 1;
-#pragma unroll
-    for (int l = 0; l < LOGB; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
-    b = j - B;
+    const bool cand = blo < bhi;
+    return 2 * (blo + ((cand && e.s0 < code) ? 1 : 0)) + ((cand && code == e.s0) ? 1 : 0);
   }
+  int j = 1;
+#pragma unroll
+  for (int l = 0; l < LOGB; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
+  const int b = j - B;
   const int sb = b < B - 1 ? b : B - 2;
   return 2 * b + (code == spl[sb] ? 1 : 0);
 }
+
+// Splitter classifier of a task with 2^LOGB buckets: one code at a time, or N codes at once
+// (all prefilter lookups, then all single-candidate refinements, so the N dependency chains of
+// shared loads overlap; the tree runs only when some code's slice holds several candidates).
+template <int LOGB, class U>
+struct SplitterClassifier {
+  const U* tree;
+  const U* spl;
+  const PrefEnt<U>* tab;
+  Pref<U> pf;
+  __device__ __forceinline__ int operator()(U code) const { return classify_fast<LOGB>(code, tree, spl, tab, pf); }
+  template <int N>
+  __device__ __forceinline__ void vec(const U (&code)[N], int (&bin)[N]) const {
+    constexpr int B = 1 << LOGB;
+    PrefEnt<U> e[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const U y = code[i] < pf.lo ? pf.lo : (code[i] > pf.hi ? pf.hi : code[i]);
+      e[i] = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
+    }
+    bool wide = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int blo = (int)(e[i].range & 0xFFFFu), bhi = (int)((e[i].range >> 16) & 0xFFFFu);
+      const bool cand = blo < bhi;
+      bin[i] = 2 * (blo + ((cand && e[i].s0 < code[i]) ? 1 : 0)) + ((cand && code[i] == e[i].s0) ? 1 : 0);
+      wide |= bhi - blo > 1;
+    }
+    if (wide) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int blo = (int)(e[i].range & 0xFFFFu), bhi = (int)((e[i].range >> 16) & 0xFFFFu);
+        if (bhi - blo > 1) {
+          int j = 1;
+#pragma unroll
+          for (int l = 0; l < LOGB; ++l) j = 2 * j + (code[i] > tree[j] ? 1 : 0);
+          const int b = j - B;
+          const int sb = b < B - 1 ? b : B - 2;
+          bin[i] = 2 * b + (code[i] == spl[sb] ? 1 : 0);
+        }
+      }
+    }
+  }
+};
 
 // Calls f(std::integral_constant<int, LOGB>) for the runtime depth (uniform per CTA).
 template <class F>
@@ -265,7 +324,7 @@ __global__ void __launch_bounds__(THREADS)
 sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_logb, int oversample,
               const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
               typename Key<KT>::U* __restrict__ tree_out, typename Key<KT>::U* __restrict__ spl_out,
-              Pref<typename Key<KT>::U>* __restrict__ pref_out, uint32_t* __restrict__ tab_out) {
+              Pref<typename Key<KT>::U>* __restrict__ pref_out, PrefEnt<typename Key<KT>::U>* __restrict__ tab_out) {
   using U = typename Key<KT>::U;
   __shared__ U s[kMaxSamples];
   const Task t = tasks[blockIdx.x];
@@ -306,7 +365,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
   const U lo = s[step - 1], hi = s[(B - 1) * step - 1];
   const U range = hi - lo;
   const int bits = range == 0 ? 0 : (int)(8 * sizeof(U)) - (sizeof(U) == 4 ? __clz((uint32_t)range) : __clzll((uint64_t)range));
-  const int shift = bits > kPrefBits ? bits - kPrefBits : 0;
+  const int shift = bits > pref_bits<U>() ? bits - pref_bits<U>() : 0;
   const int nent = (int)(range >> shift) + 1;
   if (threadIdx.x == 0) {
     Pref<U> pf;
@@ -316,7 +375,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
     pf.nent = nent;
     pref_out[blockIdx.x] = pf;
   }
-  uint32_t* tab = tab_out + (size_t)blockIdx.x * kPrefEntries;
+  PrefEnt<U>* tab = tab_out + (size_t)blockIdx.x * pref_entries<U>();
   for (int k = threadIdx.x; k < nent; k += THREADS) {
     const U first = lo + ((U)k << shift);
     const U last = k == nent - 1 ? hi : first + (((U)1 << shift) - 1);
@@ -330,7 +389,10 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
       const int m = (a2 + c2) >> 1;
       if (s[(m + 1) * step - 1] <= last) a2 = m + 1; else c2 = m;
     }
-    tab[k] = (uint32_t)a | ((uint32_t)a2 << 16);
+    PrefEnt<U> ent;
+    ent.range = (U)((uint32_t)a | ((uint32_t)a2 << 16));
+    ent.s0 = s[((a < B - 2 ? a : B - 2) + 1) * step - 1];
+    tab[k] = ent;
   }
 }
 
@@ -357,11 +419,11 @@ struct SplitterCls {
     const U* tree;
     const U* spl;
     const Pref<U>* pref;
-    const uint32_t* tab;
+    const PrefEnt<U>* tab;
   };
   struct Shared {
     U tree[kBMax], spl[kBMax];
-    uint32_t tab[kPrefEntries];
+    PrefEnt<U> tab[pref_entries<U>()];
     Pref<U> pf;
     int logb;
   };
@@ -371,7 +433,7 @@ struct SplitterCls {
     const int B = 1 << logb;
     load_splitters(sh.tree, sh.spl, p.tree + (size_t)task * kBMax, p.spl + (size_t)task * kBMax, B);
     const Pref<U> pf = p.pref[task];
-    for (int k = threadIdx.x; k < pf.nent; k += blockDim.x) sh.tab[k] = p.tab[(size_t)task * kPrefEntries + k];
+    for (int k = threadIdx.x; k < pf.nent; k += blockDim.x) sh.tab[k] = p.tab[(size_t)task * pref_entries<U>() + k];
     if (threadIdx.x == 0) {
       sh.pf = pf;
       sh.logb = logb;
@@ -384,7 +446,7 @@ struct SplitterCls {
     with_logb(sh.logb, [&](auto LB) {
       constexpr int L = decltype(LB)::value;
       const Pref<U> pf = sh.pf;
-      f([&](U code) { return classify_fast<L>(code, sh.tree, sh.spl, sh.tab, pf); });
+      f(SplitterClassifier<L, U>{sh.tree, sh.spl, sh.tab, pf});
     });
   }
 };
@@ -455,8 +517,14 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         for (int q = 0; q < NV; ++q) {
           U v[VEC];
           *reinterpret_cast<uint4*>(v) = bp[threadIdx.x + q * THREADS];
+          if (!enc) {
 #pragma unroll
-          for (int i = 0; i < VEC; ++i) count_one(v[i]);
+            for (int i = 0; i < VEC; ++i) v[i] = Key<KT>::enc(v[i]);
+          }
+          int bin[VEC];
+          classify.vec(v, bin);
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) atomicAdd(&hist[bin[i]], 1u);
         }
       } else {
         const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(wa - ws);
@@ -539,7 +607,7 @@ scan_kernel(const int32_t* __restrict__ task_nbins, const int32_t* __restrict__ 
 // run to its next free slots in the destination buffer (coalesced within runs).  Keys of an
 // equality bin written to the key buffer are final and are decoded on the way out.
 template <int KT, int VB, class CLS, int THREADS, int TILE>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 2)  // two resident CTAs per SM: at most 64 registers
 scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
                typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
                typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv,
@@ -655,16 +723,26 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         *reinterpret_cast<uint4*>(v) = reinterpret_cast<const uint4*>(bk)[vi];
 #pragma unroll
         for (int i = 0; i < VK; ++i) {
-          const int e = q * VK + i;
-          const int k = vi * VK + i;
-          const bool valid = full || (k >= k0 && k < k1);
-          code[e] = enc ? v[i] : Key<KT>::enc(v[i]);
-          if (VB) val[e] = bv[k];
-          if (valid) {
-            const int bin = classify(code[e]);
-            packed[e] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
-          } else {
-            packed[e] = 0xFFFFFFFFu;
+          v[i] = enc ? v[i] : Key<KT>::enc(v[i]);
+          code[q * VK + i] = v[i];
+          if (VB) val[q * VK + i] = bv[vi * VK + i];
+        }
+        if (full) {  // interior window: classify the vector at once, no masks
+          int bin[VK];
+          classify.vec(v, bin);
+#pragma unroll
+          for (int i = 0; i < VK; ++i)
+            packed[q * VK + i] = ((uint32_t)bin[i] << 16) | atomicAdd(&hist[bin[i]], 1u);
+        } else {
+#pragma unroll
+          for (int i = 0; i < VK; ++i) {
+            const int k = vi * VK + i;
+            if (k >= k0 && k < k1) {
+              const int bin = classify(v[i]);
+              packed[q * VK + i] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
+            } else {
+              packed[q * VK + i] = 0xFFFFFFFFu;
+            }
           }
         }
       }
@@ -687,12 +765,18 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         }
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < cnt; i += THREADS) {
+      auto write_one = [&](int i) {
         const int b = stage_b[i];
         const uint32_t o = gbase[b] + (uint32_t)i;
         const U k = bk[i];
         dstk[o] = (CLS::kEqualBins && dst_is_keys && (b & 1)) ? Key<KT>::dec(k) : k;  // equality bin: final
         if (VB) dstv[o] = bv[i];
+      };
+      if (full) {
+#pragma unroll
+        for (int r = 0; r < ITEMS; ++r) write_one(r * THREADS + threadIdx.x);
+      } else {
+        for (int i = threadIdx.x; i < cnt; i += THREADS) write_one(i);
       }
       __syncthreads();  // buffer, stage_b and hist are free again
       for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;

@@ -57,9 +57,18 @@ struct ModelCls {
     int unused;
   };
   __device__ static int setup(Shared&, const Params& p, int) { return p.nbuckets; }
+  struct Classifier {
+    const LearnedModel& m;
+    __device__ __forceinline__ int operator()(uint32_t code) const { return model_bucket(code, m); }
+    template <int N>
+    __device__ __forceinline__ void vec(const uint32_t (&code)[N], int (&bin)[N]) const {
+#pragma unroll
+      for (int i = 0; i < N; ++i) bin[i] = model_bucket(code[i], m);
+    }
+  };
   template <class F>
   __device__ static void with(const Shared&, const Params& p, F&& f) {
-    f([&](uint32_t code) { return model_bucket(code, p); });
+    f(Classifier{p});
   }
 };
 

@@ -60,7 +60,7 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
   L.spl = take((size_t)L.round_cap * kBMax * ks);
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
   L.pref = take((size_t)L.round_cap * 32);
-  L.tab = take((size_t)L.round_cap * kPrefEntries * sizeof(uint32_t));
+  L.tab = take((size_t)L.round_cap * kPrefEntriesMax * 16);
   L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
@@ -90,7 +90,7 @@ struct Shape {
   static constexpr int kSampleThreads = 512;
   // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
   // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits)
-  static constexpr int kBaseItems = KS == 4 ? 16 : 8;
+  static constexpr int kBaseItems = (KS == 4 && VB == 0) ? 32 : (KS == 4 ? 16 : 8);
   static constexpr int base_threads(int cls) { return (1024 << cls) / kBaseItems; }
   static constexpr int kMaxClass = (KS == 4 && VB <= 4) ? 4 : 3;
   static constexpr int kMaxCap = 1024 << kMaxClass;
@@ -146,7 +146,7 @@ class PlainSorter {
     spl_ = reinterpret_cast<U*>(ws + L_.spl);
     children_ = reinterpret_cast<uint2*>(ws + L_.children);
     pref_ = reinterpret_cast<Pref<U>*>(ws + L_.pref);
-    tab_ = reinterpret_cast<uint32_t*>(ws + L_.tab);
+    tab_ = reinterpret_cast<PrefEnt<U>*>(ws + L_.tab);
     base_items_ = reinterpret_cast<Item*>(ws + L_.base_items);
     copy_items_ = reinterpret_cast<Item*>(ws + L_.copy_items);
     fb_items_ = reinterpret_cast<Item*>(ws + L_.fb_items);
@@ -205,7 +205,7 @@ class PlainSorter {
   uint32_t* counts_;
   uint2* children_;
   Pref<U>* pref_;
-  uint32_t* tab_;
+  PrefEnt<U>* tab_;
   Item *base_items_, *copy_items_, *fb_items_;
   cudaStream_t st_;
 
