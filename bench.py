@@ -12,7 +12,8 @@ then K steps, each bracketed by CUDA events on the sorting stream; the input is 
 a pristine device copy and L2 is flushed (a 512 MiB write) between steps, outside the events.
 
 Extra keys: `roofline` (dominant kernel: algorithmic bytes / its event-timed duration vs the
-measured HBM copy bandwidth), `cpu_baseline` (the CPU oracle on one host core, on a bounded
+measured HBM copy bandwidth; `roofline.path`: the same for the whole sort, bytes per pass times
+passes over the step time), `cpu_baseline` (the CPU oracle on one host core, on a bounded
 sample), `e2e` (same metric through the host-buffer C-ABI call pdq_sort_host, copies included),
 `clocks` (nvidia-smi sampled during the timed region), `gpu_launches` (library kernels launched
 in the timed region).
@@ -105,7 +106,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv",
-                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -269,7 +270,7 @@ def dtype_name(name: str) -> str:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uniform_i32_2p28", choices=sorted(WORKLOADS))
@@ -398,6 +399,14 @@ def bench_gpu(args, rank: int, world: int) -> None:
                     "share_of_step": dms / max(1e-9, sum(v[0] for v in prof.values())),
                     "kernels": {k: {"ms": v[0], "launches": v[1], "alg_bytes": v[2]}
                                 for k, v in prof.items()}}
+        # whole-sort roofline: bytes the method must move (each distribution level, base pass,
+        # copy, reversal and probe), the histogram re-read of the count kernels being overhead
+        # rather than credit; divided by the timed step time
+        path_bytes = sum(v[2] for k, v in prof.items() if "count" not in k)
+        step_ms = total_ms / args.steps
+        roofline["path"] = {"algorithmic_bytes_per_step": path_bytes, "ms_per_step": step_ms,
+                            "achieved": path_bytes / (step_ms * 1e-3) / 1e9,
+                            "frac": path_bytes / (step_ms * 1e-3) / 1e9 / peak}
 
     # end to end through the host-buffer call (pinned host memory, copies inside the timing)
     e2e = None
