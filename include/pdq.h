@@ -134,6 +134,31 @@ int pdq_sort_keys_learned(void* d_keys, int64_t n, pdq_dtype key_dtype, void* d_
                           void* cuda_stream, const pdq_tuning* tuning, pdq_stats* stats);
 size_t pdq_workspace_bytes_learned(int64_t n);
 
+/* Autotuner.  Picks, for the shape of one call, the bucket count per distribution level
+ * (log2_buckets), the shared-memory base-case size (base_capacity; on the segmented path the
+ * persistent CTA size seg_block, which fixes the size up to which a segment is sorted in shared
+ * memory) by timing a fixed candidate grid on a scratch copy of the caller's input with CUDA
+ * events, and records the fastest for the call's shape class: (plain or segmented, key type,
+ * value_bytes, ceil(log2 n), ceil(log2 num_segments)).  Later pdq_sort_keys / pdq_sort_pairs /
+ * pdq_sort_segmented / pdq_sort_host calls of that class that pass tuning = NULL use the recorded
+ * tuning (an explicit tuning always wins).  The table is per process and lives until exit or
+ * pdq_autotune_reset().
+ *   d_keys, d_vals, value_bytes, d_offsets, num_segments (0 = plain path), n, key_dtype: the input
+ *                as it would be passed to the sort; it is only read (never modified).
+ *   d_scratch  : device memory of scratch_bytes >= pdq_autotune_scratch_bytes(...) bytes, 256-byte
+ *                aligned (a copy of the keys and values plus a sort workspace).
+ *   best       : nullable; receives the chosen tuning.  best_ms: nullable; its time in ms.
+ * The call synchronises cuda_stream after every candidate; it takes a few dozen sorts' time.
+ * Errors as for the sorts; on error nothing is recorded. */
+size_t pdq_autotune_scratch_bytes(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes);
+int pdq_autotune(const void* d_keys, const void* d_vals, int value_bytes, const int64_t* d_offsets,
+                 int64_t num_segments, int64_t n, pdq_dtype key_dtype, void* d_scratch, size_t scratch_bytes,
+                 void* cuda_stream, pdq_tuning* best, float* best_ms);
+/* 1 and *out = the recorded tuning if pdq_autotune recorded one for this shape class, else 0. */
+int pdq_autotune_lookup(int64_t n, int64_t num_segments, pdq_dtype key_dtype, int value_bytes, pdq_tuning* out);
+/* Forget every recorded tuning. */
+void pdq_autotune_reset(void);
+
 /* Test probes of the learned model (parity of the hand-written forward/backward with a CPU
  * reference).  theta = [alpha(16), omega(16), c(16)]: a = softmax(alpha), w = exp(omega),
  * F(x) = sum_j a_j sat(w_j ((x - mu) / sigma - c_j)).

@@ -105,6 +105,15 @@ def lib() -> ctypes.CDLL:
             L.pdq_profile_read.restype = i32
             L.pdq_profile_reset.argtypes = []
             L.pdq_profile_reset.restype = None
+            L.pdq_autotune_scratch_bytes.argtypes = [i64, i64, i32, i32]
+            L.pdq_autotune_scratch_bytes.restype = sz
+            L.pdq_autotune.argtypes = [vp, vp, i32, vp, i64, i64, i32, vp, sz, vp, P(Tuning),
+                                       P(ctypes.c_float)]
+            L.pdq_autotune.restype = i32
+            L.pdq_autotune_lookup.argtypes = [i64, i64, i32, i32, P(Tuning)]
+            L.pdq_autotune_lookup.restype = i32
+            L.pdq_autotune_reset.argtypes = []
+            L.pdq_autotune_reset.restype = None
             _lib = L
         return _lib
 
@@ -211,6 +220,46 @@ def pdq_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, vals: torch.Te
                                     offsets.data_ptr(), nseg, n, dt, ws.data_ptr(), ws.numel(),
                                     _stream_ptr(stream), _tuning(tuning), ctypes.byref(st)))
     return st.as_dict()
+
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {name: int(getattr(t, name)) for name, _ in Tuning._fields_}
+
+
+def pdq_autotune(keys: torch.Tensor, vals: torch.Tensor | None = None, offsets: torch.Tensor | None = None,
+                 key_dtype: int | None = None, stream=None) -> tuple[dict, float]:
+    """Time the candidate tunings on a scratch copy of ``keys`` (and ``vals``; per segment of
+    ``offsets`` when given) and record the fastest for this call shape; later sorts of the same
+    shape class that pass no tuning use it.  Returns (tuning, milliseconds)."""
+    _require_cuda(keys, "keys")
+    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    vb = vals.element_size() if vals is not None else 0
+    n = keys.numel()
+    nseg = max(0, offsets.numel() - 1) if offsets is not None else 0
+    need = lib().pdq_autotune_scratch_bytes(n, nseg, dt, vb)
+    if need == 0:
+        raise PdqError(-1, "no autotune scratch size for these arguments")
+    scratch = torch.empty(need, dtype=torch.uint8, device=keys.device)
+    best = Tuning()
+    ms = ctypes.c_float(0.0)
+    _check(lib().pdq_autotune(keys.data_ptr(), vals.data_ptr() if vals is not None else None, vb,
+                              offsets.data_ptr() if offsets is not None else None, nseg, n, dt,
+                              scratch.data_ptr(), scratch.numel(), _stream_ptr(stream), ctypes.byref(best),
+                              ctypes.byref(ms)))
+    return _tuning_dict(best), float(ms.value)
+
+
+def pdq_autotune_lookup(n: int, key_dtype: int, value_bytes: int = 0, num_segments: int = 0) -> dict | None:
+    """The tuning recorded for this call shape, or None."""
+    t = Tuning()
+    if lib().pdq_autotune_lookup(n, num_segments, int(key_dtype), value_bytes, ctypes.byref(t)):
+        return _tuning_dict(t)
+    return None
+
+
+def pdq_autotune_reset() -> None:
+    """Forget every recorded tuning."""
+    lib().pdq_autotune_reset()
 
 
 def pdq_sort_host(h_keys: torch.Tensor, d_keys: torch.Tensor, workspace: torch.Tensor,

@@ -218,6 +218,8 @@ static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int d
   a.ws_bytes = ws_bytes;
   a.stream = static_cast<cudaStream_t>(stream);
   a.num_sms = num_sms();
+  pdq_tuning tuned;
+  if (!tuning && autotune_lookup(false, dt, value_bytes, n, 0, &tuned)) tuning = &tuned;
   int rc = make_tuning(tuning, &a.tune);
   if (rc) return rc;
   switch (value_bytes) {
@@ -317,6 +319,8 @@ int pdq_sort_segmented(void* d_keys, void* d_vals, int value_bytes, const int64_
   a.ws_bytes = ws_bytes;
   a.stream = static_cast<cudaStream_t>(cuda_stream);
   a.num_sms = num_sms();
+  pdq_tuning tuned;
+  if (!tuning && autotune_lookup(true, key_dtype, value_bytes, n, num_segments, &tuned)) tuning = &tuned;
   int rc = make_tuning(tuning, &a.tune);
   if (rc) return rc;
   switch (value_bytes) {

@@ -46,6 +46,7 @@ struct SegState {
   unsigned long long bad_splits;
   unsigned long long max_depth;
   unsigned long long never_set;     // written by nobody: the wait-injection hook waits on it
+  unsigned long long n_blist[kBaseClasses];  // entries appended to each base-size class list
 };
 
 struct SegLists {
@@ -56,6 +57,11 @@ struct SegLists {
   int64_t fb_cap;
   Item* huge;
   int64_t huge_cap;
+  // buckets of at most max_base elements, binned by size class (1024 << c) for the
+  // class-shaped base-sort kernels that run after the persistent kernel
+  Item* blist[kBaseClasses];
+  int64_t bcap[kBaseClasses];
+  int64_t max_base;
 };
 
 struct SegParams {
@@ -84,6 +90,16 @@ __device__ __forceinline__ bool list_push(unsigned long long* counter, Item* lis
   if ((int64_t)k >= cap) return false;
   list[k] = it;
   return true;
+}
+
+__device__ __forceinline__ int seg_base_class(int64_t m) {
+  return m <= 1024 ? 0 : (m <= 2048 ? 1 : (m <= 4096 ? 2 : (m <= 8192 ? 3 : 4)));
+}
+
+// Appends a base-size bucket to its size-class list; false when that list is full.
+__device__ __forceinline__ bool seg_base_push(SegState* st, const SegLists& L, const Item& it) {
+  const int c = seg_base_class(it.size);
+  return list_push(&st->n_blist[c], L.blist[c], L.bcap[c], it);
 }
 
 // Claims the next published slot of queue qi (thread 0 only).  0: got a task, 1: empty,
@@ -138,7 +154,8 @@ __global__ void seg_bin_kernel(const int64_t* __restrict__ offsets, int64_t nseg
     t.attempt = 0;
     t.depth = 0;
     Item it{b, (uint32_t)size, (uint16_t)kBufKeys, 0};
-    if (size <= cap) {
+    if (size <= L.max_base && seg_base_push(st, L, it)) continue;
+    if (size <= cap) {  // its class list is full: the persistent kernel sorts it
       t.kind = kSegBase;
       if (!seg_push(st, L, 1, t) && !list_push(&st->n_fallback, L.fallback, L.fb_cap, it))
         atomicOr(&st->error, 2ull);
@@ -155,23 +172,38 @@ __global__ void seg_bin_kernel(const int64_t* __restrict__ offsets, int64_t nseg
 }
 
 // ------------------------------------------------------------------ one-CTA distribution level
+// Elements per streamed tile of the one-CTA partition (two slots of it hold the 4096 samples).
+constexpr int kSegTile = 2048;
+
 template <int KT, int VB, int THREADS>
 __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, typename Key<KT>::U* keys,
                               typename Val<VB>::T* vals, typename Key<KT>::U* tmpk, typename Val<VB>::T* tmpv,
                               unsigned char* smem, uint32_t* wtmp, SegState* st, const SegLists& L) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
-  U* s = reinterpret_cast<U*>(smem);
-  U* s_tree = s + kMaxSamples;
+  constexpr int T = kSegTile;      // elements per streamed tile
+  constexpr int ITP = T / THREADS;  // elements per thread per tile
+  static_assert(T % THREADS == 0 && 2 * T >= kMaxSamples, "tile shape");
+  // shared memory: two stream slots (keys, then values; the samples live there first), tree,
+  // splitters, staged tile (keys, values), per-bin totals / cursors / tile counts, staged bins
+  U* kslot = reinterpret_cast<U*>(smem);
+  V* vslot = reinterpret_cast<V*>(kslot + 2 * T);
+  U* s = kslot;
+  U* s_tree = reinterpret_cast<U*>(reinterpret_cast<unsigned char*>(vslot) + (size_t)2 * T * VB);
   U* s_spl = s_tree + kBMax;
-  uint32_t* hist = reinterpret_cast<uint32_t*>(s_spl + kBMax);
-  uint32_t* curs = hist + kBinsMax;
+  U* sk = s_spl + kBMax;
+  V* sv = reinterpret_cast<V*>(sk + T);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(sv) + (size_t)T * VB);
+  uint32_t* curs = hist + kBinsMax;  // global write cursor per bin
+  uint32_t* th = curs + kBinsMax;    // tile count, then tile start, per bin
+  uint16_t* sb = reinterpret_cast<uint16_t*>(th + kBinsMax);
   const int tid = threadIdx.x;
   const int64_t size = t.size;
-  // buckets: expected child a quarter of the base capacity
+  // buckets: expected child a quarter of the largest base-size bucket
   int logb = 1;
   {
-    const int64_t want = (size + cap / 4 - 1) / (cap / 4);
+    const int64_t q = L.max_base / 4;
+    const int64_t want = (size + q - 1) / q;
     while ((int64_t(1) << logb) < want && logb < prm.max_logb) ++logb;
   }
   const int B = 1 << logb;
@@ -212,28 +244,101 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
   for (int j = 1 + tid; j < B; j += THREADS) s_tree[j] = s[(eytz_inorder(j, logb) + 1) * step - 1];
   for (int b = tid; b < nb; b += THREADS) hist[b] = 0;
   __syncthreads();
+  // Both passes stream the segment through the two slots with cp.async: tile k+1 is in flight
+  // while tile k is processed (every thread commits one group per tile, possibly empty).
+  auto fetch = [&](int64_t t0, int slot, bool with_vals) {
+#pragma unroll
+    for (int e = 0; e < ITP; ++e) {
+      const int j = e * THREADS + tid;
+      const int64_t i = t0 + j;
+      if (i < size) {
+        cp_async<sizeof(U)>(&kslot[slot * T + j], &srck[i]);
+        if constexpr (VB > 0) {
+          if (with_vals) cp_async<VB>(&vslot[slot * T + j], &srcv[i]);
+        }
+      }
+    }
+    cp_async_commit();
+  };
   // count
   with_logb(logb, [&](auto LB) {
     constexpr int LL = decltype(LB)::value;
-    for (int64_t i = tid; i < size; i += THREADS) {
-      const U x = srck[i];
-      atomicAdd(&hist[classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+    fetch(0, 0, false);
+    int k = 0;
+    for (int64_t t0 = 0; t0 < size; t0 += T, ++k) {
+      if (t0 + T < size) fetch(t0 + T, (k + 1) & 1, false);
+      else cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      const U* kb = kslot + (k & 1) * T;
+#pragma unroll
+      for (int e = 0; e < ITP; ++e) {
+        const int j = e * THREADS + tid;
+        if (t0 + j < size) {
+          const U x = kb[j];
+          atomicAdd(&hist[classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+        }
+      }
+      __syncthreads();
     }
+    cp_async_wait<0>();
   });
   __syncthreads();
   block_exclusive_scan<THREADS>(hist, curs, nb, wtmp);  // curs := bin starts
-  // scatter (equality bins written to the key buffer are final: decoded on the way)
+  // scatter, one tile at a time: rank inside the tile per bin, stage grouped by bin in shared
+  // memory, then write each bin's run of the tile at its cursor (contiguous stores); equality
+  // bins written to the key buffer are final, so they are decoded on the way
   const bool dst_is_keys = !from_keys;
   with_logb(logb, [&](auto LB) {
     constexpr int LL = decltype(LB)::value;
-    for (int64_t i = tid; i < size; i += THREADS) {
-      const U x = srck[i];
-      const U code = enc ? x : Key<KT>::enc(x);
-      const int bin = classify_t<LL>(code, s_tree, s_spl);
-      const uint32_t p = atomicAdd(&curs[bin], 1u);
-      dstk[p] = (dst_is_keys && (bin & 1)) ? Key<KT>::dec(code) : code;
-      if (VB) dstv[p] = srcv[i];
+    fetch(0, 0, true);
+    int k = 0;
+    for (int64_t t0 = 0; t0 < size; t0 += T, ++k) {
+      const int cnt = (int)(size - t0 < T ? size - t0 : T);
+      for (int b = tid; b < nb; b += THREADS) th[b] = 0;
+      if (t0 + T < size) fetch(t0 + T, (k + 1) & 1, true);
+      else cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      const U* kb = kslot + (k & 1) * T;
+      const V* vb = vslot + (k & 1) * T;
+      int bin[ITP];
+      uint32_t rk[ITP];
+#pragma unroll
+      for (int e = 0; e < ITP; ++e) {
+        const int j = e * THREADS + tid;
+        if (j < cnt) {
+          const U x = kb[j];
+          bin[e] = classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl);
+          rk[e] = atomicAdd(&th[bin[e]], 1u);
+        }
+      }
+      __syncthreads();
+      block_exclusive_scan<THREADS>(th, th, nb, wtmp);  // th := tile starts
+#pragma unroll
+      for (int e = 0; e < ITP; ++e) {
+        const int j = e * THREADS + tid;
+        if (j < cnt) {
+          const U x = kb[j];
+          const U code = enc ? x : Key<KT>::enc(x);
+          const uint32_t p = th[bin[e]] + rk[e];
+          sk[p] = (dst_is_keys && (bin[e] & 1)) ? Key<KT>::dec(code) : code;
+          sb[p] = (uint16_t)bin[e];
+          if (VB) sv[p] = vb[j];
+        }
+      }
+      __syncthreads();
+      for (int j = tid; j < cnt; j += THREADS) {
+        const int b = sb[j];
+        const uint32_t g = curs[b] + (uint32_t)j - th[b];
+        dstk[g] = sk[j];
+        if (VB) dstv[g] = sv[j];
+      }
+      __syncthreads();
+      for (int b = tid; b < nb; b += THREADS) curs[b] += (b + 1 < nb ? th[b + 1] : (uint32_t)cnt) - th[b];
+      __syncthreads();
     }
+    cp_async_wait<0>();
   });
   __syncthreads();
   // children
@@ -253,7 +358,8 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
     c.enc = 1;
     c.attempt = t.attempt + 1;
     c.depth = t.depth + 1;
-    if ((int64_t)cnt <= cap) {
+    if ((int64_t)cnt <= L.max_base && seg_base_push(st, L, it)) continue;
+    if ((int64_t)cnt <= cap) {  // its class list is full: the persistent kernel sorts it
       c.kind = kSegBase;
       c.bad_left = t.bad_left;
       if (!seg_push(st, L, 1, c) && !list_push(&st->n_fallback, L.fallback, L.fb_cap, it))
@@ -289,7 +395,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
 
 // ------------------------------------------------------------------ persistent kernel
 template <int KT, int VB, int THREADS, int ITEMS>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, 512 / THREADS)
 seg_persistent_kernel(typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
                       typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv,
                       SegState* st, SegLists L, SegParams prm) {
@@ -358,10 +464,30 @@ seg_persistent_kernel(typename Key<KT>::U* __restrict__ keys, typename Val<VB>::
   }
 }
 
+// ------------------------------------------------------------------ class-shaped base sorts
+// After the persistent kernel: every CTA sorts list entries blockIdx.x, blockIdx.x + gridDim.x,
+// ... of one size class in shared memory, decoding into the key buffer.  The entry count is read
+// on the device, so the launch needs no host round trip and is captured with the rest.
+template <int KT, int VB, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+seg_base_list_kernel(const Item* __restrict__ list, const unsigned long long* __restrict__ count, int64_t cap,
+                     typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
+                     typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t c = (int64_t)*count;
+  const int64_t m = c < cap ? c : cap;
+  for (int64_t k = blockIdx.x; k < m; k += gridDim.x) {
+    const Item it = list[k];
+    base_sort_block<KT, VB, THREADS, ITEMS>(it, keys, vals, tmpk, tmpv, kBufKeys, 1, smem);
+    __syncthreads();
+  }
+}
+
 template <int KS, int VB, int THREADS, int ITEMS>
 constexpr size_t seg_smem() {
   constexpr size_t base = base_sort_smem<KS, VB, THREADS, ITEMS>();
-  constexpr size_t part = (size_t)(kMaxSamples + 2 * kBMax) * KS + 2 * kBinsMax * sizeof(uint32_t);
+  constexpr size_t part = (size_t)(3 * kSegTile + 2 * kBMax) * KS + (size_t)3 * kSegTile * VB +
+                         3 * kBinsMax * sizeof(uint32_t) + (size_t)kSegTile * 2;
   return base > part ? base : part;
 }
 

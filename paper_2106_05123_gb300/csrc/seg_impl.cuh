@@ -16,6 +16,8 @@ constexpr int64_t kSegPersistMax = int64_t(1) << 20;  // larger segments use the
 struct SegLayout {
   size_t tmpk, tmpv, state, slots0, ready0, slots1, ready1, fb, huge, total;
   int64_t cap0, cap1, fb_cap, huge_cap;
+  size_t blist[kBaseClasses];
+  int64_t bcap[kBaseClasses];
 };
 
 inline SegLayout make_seg_layout(int64_t n, int64_t nseg, int ks, int vb) {
@@ -41,6 +43,13 @@ inline SegLayout make_seg_layout(int64_t n, int64_t nseg, int ks, int vb) {
   L.ready1 = take((size_t)L.cap1 * sizeof(uint32_t));
   L.fb = take((size_t)L.fb_cap * sizeof(Item));
   L.huge = take((size_t)L.huge_cap * sizeof(Item));
+  // size-class lists: an entry of class c >= 1 has more than 512 << c elements, so at most
+  // n / (512 << c) of them exist; class 0 gets one entry per segment plus n / 256 (a full list
+  // sends further buckets to the persistent kernel's own base queue)
+  for (int c = 0; c < kBaseClasses; ++c) {
+    L.bcap[c] = c == 0 ? nseg + n / 256 + 1024 : n / ((int64_t)512 << c) + 1;
+    L.blist[c] = take((size_t)L.bcap[c] * sizeof(Item));
+  }
   L.total = off;
   return L;
 }
@@ -80,6 +89,11 @@ class SegSorter {
     lists.fb_cap = L.fb_cap;
     lists.huge = reinterpret_cast<Item*>(ws + L.huge);
     lists.huge_cap = L.huge_cap;
+    for (int c = 0; c < kBaseClasses; ++c) {
+      lists.blist[c] = reinterpret_cast<Item*>(ws + L.blist[c]);
+      lists.bcap[c] = c <= S::kMaxClass ? L.bcap[c] : 0;
+    }
+    lists.max_base = S::kMaxCap;
     SegParams prm;
     prm.max_logb = a_.tune.logb;
     prm.oversample = a_.tune.oversample;
@@ -102,6 +116,8 @@ class SegSorter {
     PDQ_CUDA(cudaStreamSynchronize(a_.stream));
     stats_.equal_buckets = (int64_t)h.equal_buckets;
     stats_.base_buckets = (int64_t)h.base_buckets;
+    for (int c = 0; c <= S::kMaxClass; ++c)
+      stats_.base_buckets += (int64_t)std::min<unsigned long long>(h.n_blist[c], (unsigned long long)L.bcap[c]);
     stats_.bad_splits = (int64_t)h.bad_splits;
     stats_.passes = (int64_t)h.max_depth;
     stats_.fallback_buckets = (int64_t)fb.size();
@@ -154,6 +170,36 @@ class SegSorter {
  private:
   SegArgs a_;
 
+  using S = Shape<KS, VB>;
+
+  // Class c of the size-class base sorts: the plain path's base-sort shape for that class.
+  template <int CLS>
+  int configure_class(int* grid) {
+    constexpr int T = S::base_threads(CLS);
+    constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
+    static bool configured = false;
+    if (!configured) {
+      PDQ_CUDA(cudaFuncSetAttribute(seg_base_list_kernel<KT, VB, T, S::kBaseItems>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      configured = true;
+    }
+    int per_sm = 0;
+    PDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_base_list_kernel<KT, VB, T, S::kBaseItems>,
+                                                           T, smem));
+    *grid = a_.num_sms * (per_sm < 1 ? 1 : per_sm);
+    return PDQ_OK;
+  }
+  template <int CLS>
+  int launch_class(int grid, const SegLists& lists, SegState* st, U* keys, V* vals, U* tmpk, V* tmpv,
+                   cudaStream_t s) {
+    constexpr int T = S::base_threads(CLS);
+    constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
+    seg_base_list_kernel<KT, VB, T, S::kBaseItems><<<grid, T, smem, s>>>(
+        lists.blist[CLS], &st->n_blist[CLS], lists.bcap[CLS], keys, vals, tmpk, tmpv);
+    PDQ_LAUNCHED("seg_base_list");
+    return PDQ_OK;
+  }
+
   template <int T>
   int launch(const SegLayout& L, SegState* st, const SegLists& lists, const SegParams& prm) {
     constexpr size_t smem = seg_smem<KS, VB, T, ITEMS>();
@@ -162,6 +208,17 @@ class SegSorter {
       PDQ_CUDA(cudaFuncSetAttribute(seg_persistent_kernel<KT, VB, T, ITEMS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       configured = true;
+    }
+    int cls_grid[kBaseClasses] = {0, 0, 0, 0, 0};
+    {
+      int rc = configure_class<0>(&cls_grid[0]);
+      if (!rc) rc = configure_class<1>(&cls_grid[1]);
+      if (!rc) rc = configure_class<2>(&cls_grid[2]);
+      if (!rc) rc = configure_class<3>(&cls_grid[3]);
+      if constexpr (S::kMaxClass >= 4) {
+        if (!rc) rc = configure_class<4>(&cls_grid[4]);
+      }
+      if (rc) return rc;
     }
     int per_sm = 0;
     PDQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_persistent_kernel<KT, VB, T, ITEMS>, T, smem));
@@ -181,6 +238,14 @@ class SegSorter {
       PDQ_LAUNCHED("seg_bin");
       seg_persistent_kernel<KT, VB, T, ITEMS><<<grid, T, smem, s>>>(keys, vals, tmpk, tmpv, st, lists, prm);
       PDQ_LAUNCHED("seg_persistent");
+      int rc = launch_class<0>(cls_grid[0], lists, st, keys, vals, tmpk, tmpv, s);
+      if (!rc) rc = launch_class<1>(cls_grid[1], lists, st, keys, vals, tmpk, tmpv, s);
+      if (!rc) rc = launch_class<2>(cls_grid[2], lists, st, keys, vals, tmpk, tmpv, s);
+      if (!rc) rc = launch_class<3>(cls_grid[3], lists, st, keys, vals, tmpk, tmpv, s);
+      if constexpr (S::kMaxClass >= 4) {
+        if (!rc) rc = launch_class<4>(cls_grid[4], lists, st, keys, vals, tmpk, tmpv, s);
+      }
+      if (rc) return rc;
       return PDQ_OK;
     };
     GraphKey key{KT, VB, T, prm.max_logb, prm.oversample, prm.bad0, prm.inject_wait, prm.wait_ns,

@@ -70,4 +70,7 @@ size_t learned_workspace_bytes(int64_t n);
 template <int KT, int VB>
 size_t seg_workspace_bytes_impl(int64_t n, int64_t nseg);
 
+// Tuning recorded by pdq_autotune for a call shape (autotune.cu); false when none was recorded.
+bool autotune_lookup(bool seg, int dt, int vb, int64_t n, int64_t nseg, pdq_tuning* out);
+
 }  // namespace pdq

@@ -92,4 +92,19 @@ struct TileGeom {
   __device__ __forceinline__ int64_t edge(int64_t s, int j) const { return j < head ? s + j : ae + (j - head); }
 };
 
+// Asynchronous global -> shared copies of N = 4, 8 or 16 bytes per thread (cp.async, no register
+// staging); commit closes this thread's group, wait<K> blocks until at most K of its groups are
+// still in flight.  Visibility to other threads needs a barrier after the wait.
+template <int N>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gsrc) {
+  static_assert(N == 4 || N == 8 || N == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(smem_dst)), "l"(gsrc), "n"(N)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
 }  // namespace pdq

@@ -70,3 +70,21 @@ def test_argument_errors_need_no_device(L):
     bad = pdq.Tuning(log2_buckets=10)
     assert L.pdq_sort_keys(ctypes.c_void_p(4096), 10, 0, ctypes.c_void_p(4096), 1 << 20, None,
                            ctypes.byref(bad), ctypes.byref(st)) in (-1, -3)
+
+
+def test_autotune_host_logic(L):
+    # scratch = keys copy + values copy + sort workspace, each 256-byte aligned
+    ws = L.pdq_workspace_bytes(1000, 0, 0, 4)
+    sc = L.pdq_autotune_scratch_bytes(1000, 0, 0, 4)
+    assert sc == 4096 + 4096 + ws
+    assert L.pdq_autotune_scratch_bytes(1000, 0, 9, 0) == 0       # unknown dtype
+    assert L.pdq_autotune_scratch_bytes(1000, 0, 0, 3) == 0       # bad value width
+    assert L.pdq_autotune_scratch_bytes(1000, 7, 2, 0) >= 1000 * 8  # segmented
+    L.pdq_autotune_reset()
+    assert L.pdq_autotune_lookup(1000, 0, 0, 0, None) == 0
+    # argument errors answer on the host, before any device work
+    assert L.pdq_autotune(None, None, 0, None, 0, 1000, 0, None, 0, None, None, None) == -1
+    assert L.pdq_autotune(None, None, 0, None, 0, 1000, 9, None, 0, None, None, None) == -2
+    assert L.pdq_autotune(ctypes.c_void_p(256), None, 0, None, 0, 1000, 0, None, 0, None, None, None) == -3
+    assert L.pdq_autotune(ctypes.c_void_p(256), None, 0, None, 5, 1000, 0, ctypes.c_void_p(256), 1 << 30,
+                          None, None, None) == -1  # segmented without offsets
