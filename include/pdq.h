@@ -166,8 +166,9 @@ void pdq_autotune_reset(void);
  *   h_out[48] = sum of 0.5 (F(x_i) - t_i)^2; d_ws: >= 512 bytes of device scratch.
  * pdq_learned_train: trains on the sorted sample d_xs[0..m) (targets (i + 0.5) / m) for `steps`
  *   Adam steps of `batch` points; returns theta, [mu, sigma, first loss, last loss] and the
- *   folded model's w, t, a (3 x 16 floats: h_j = sat(w_j (x - t_j))); d_ws: >= 1024 bytes of
- *   device scratch. */
+ *   folded model's w, t, a (3 x 16 floats: h_j = sat(w_j (x - t_j))); d_ws: >= 4096 bytes of
+ *   device scratch, 256-byte aligned.  The training runs as one cooperative launch of one CTA
+ *   per SM whose grid barriers are bounded (1 s): PDQ_ERR_TIMEOUT if one gives up. */
 int pdq_learned_loss_grad(const float* d_x, const float* d_targets, int64_t m, const float* h_theta,
                           float mu, float sigma, float* h_out, void* d_ws, void* cuda_stream);
 int pdq_learned_train(const float* d_xs, int64_t m, int steps, int batch, float lr, void* d_ws,

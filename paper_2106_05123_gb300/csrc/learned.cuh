@@ -79,6 +79,8 @@ struct TrainOut {
   float mu, sigma;
   float loss_first, loss_last;  // minibatch loss of the first and last step
   LearnedModel model;
+  int status;                   // 0: trained; 1: a grid barrier gave up (model = last update)
+  int pad[3];
 };
 
 // Forward of one point in the training parametrisation; fills h (hidden outputs), z (ramp
@@ -160,17 +162,60 @@ __device__ __forceinline__ void block_sum_params(float* g, float* red) {
 
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7F800000u) != 0x7F800000u; }
 
-// One CTA: initialise from sample quantiles, run `steps` Adam steps on minibatches of `batch`
-// points of the sorted sample xs[0..m), write the trained and folded model.
+// Cross-CTA state of one training run (zeroed before the launch): gradient sums of three
+// consecutive steps (rotating, so that a buffer is cleared two steps before it is refilled) and
+// the grid barrier.
+struct TrainSync {
+  float gsum[3][kParams + 1];
+  unsigned int count, gen, err, pad;
+};
+
+// Grid-wide barrier over all CTAs of a cooperative launch, bounded in time: false (for every
+// thread of the CTA) when the other CTAs did not arrive within `limit_ns`.
+__device__ __forceinline__ bool grid_barrier(TrainSync* sy, uint64_t limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &sy->gen;
+    const unsigned int g = *vgen;  // cannot change before this CTA arrives
+    __threadfence();
+    if (atomicAdd(&sy->count, 1u) == gridDim.x - 1) {
+      atomicExch(&sy->count, 0u);
+      __threadfence();
+      atomicAdd(&sy->gen, 1u);
+    } else {
+      const uint64_t t0 = global_ns();
+      while (*vgen == g) {
+        if (global_ns() - t0 > limit_ns) {
+          ok = 0;
+          atomicOr(&sy->err, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Training, one CTA per SM (cooperative launch): every CTA initialises the same parameters from
+// the sample quantiles; per Adam step each CTA sums the gradient of its share of a minibatch of
+// `batch` points of the sorted sample xs[0..m), the sums meet in global memory, and after a grid
+// barrier every CTA applies the same Adam update to its own copy of the parameters (identical
+// arithmetic on identical inputs keeps the copies equal).  CTA 0 writes the trained and folded
+// model.
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 learned_train_kernel(const float* __restrict__ xs, int64_t m, int steps, int batch, float lr, uint64_t seed,
-                     TrainOut* out) {
+                     TrainOut* out, TrainSync* sy) {
   __shared__ float theta[kParams], madam[kParams], vadam[kParams];
   __shared__ float c0[kHidden], cs[kHidden], dpos[kHidden];  // ramp start = c0 + cs * dpos
   __shared__ float pa[kHidden], pw[kHidden], pc[kHidden];    // this step's a, w, c
   __shared__ float red[kParams + 1];
-  __shared__ float s_mu, s_sigma;
+  __shared__ float s_mu, s_sigma, s_loss;
   __shared__ int64_t s_lo, s_hi;  // finite range of the sorted sample
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -213,6 +258,7 @@ learned_train_kernel(const float* __restrict__ xs, int64_t m, int steps, int bat
   __syncthreads();
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   float loss_first = 0.f, loss_last = 0.f;
+  bool ok = true;
   for (int step = 0; step < steps && hi > lo; ++step) {
     if (tid < kHidden) {
       float amax = theta[0];
@@ -227,16 +273,22 @@ learned_train_kernel(const float* __restrict__ xs, int64_t m, int steps, int bat
     float g[kParams + 1];
 #pragma unroll
     for (int i = 0; i <= kParams; ++i) g[i] = 0.f;
-    int cnt = 0;
-    for (int k = tid; k < batch; k += THREADS) {
+    for (int k = blockIdx.x * THREADS + tid; k < batch; k += gridDim.x * THREADS) {
       const uint64_t r = mix64(seed + ((uint64_t)step * (uint64_t)batch + (uint64_t)k + 1) * 0x9E3779B97F4A7C15ull);
       const int64_t i = lo + (int64_t)(r % (uint64_t)(hi - lo));
       const float target = ((float)i + 0.5f) / (float)m;
       g[kParams] += model_point_grad_pre(pa, pw, pc, (xs[i] - mu) / sigma, target, g);
-      ++cnt;
     }
-    (void)cnt;
     block_sum_params<THREADS>(g, red);
+    float* gs = sy->gsum[step % 3];
+    if (tid <= kParams) atomicAdd(&gs[tid], red[tid]);
+    if (!grid_barrier(sy, 1000000000ull)) {
+      ok = false;
+      break;
+    }
+    if (blockIdx.x == 0 && tid <= kParams) sy->gsum[(step + 2) % 3][tid] = 0.f;  // refilled at step + 2
+    if (tid <= kParams) red[tid] = __ldcg(&gs[tid]);
+    __syncthreads();
     if (tid < kParams) {
       const bool start = tid >= 2 * kHidden;  // ramp starts are trained in units of their width
       const int j = tid - 2 * kHidden;
@@ -253,16 +305,18 @@ learned_train_kernel(const float* __restrict__ xs, int64_t m, int steps, int bat
         theta[tid] -= delta;
       }
     }
-    if (step == 0) loss_first = red[kParams] / (float)batch;
-    loss_last = red[kParams] / (float)batch;
+    if (tid == 0) s_loss = red[kParams] / (float)batch;
     __syncthreads();
+    if (step == 0) loss_first = s_loss;
+    loss_last = s_loss;
   }
-  if (tid == 0) {
+  if (blockIdx.x == 0 && tid == 0) {
     for (int i = 0; i < kParams; ++i) out->theta[i] = theta[i];
     out->mu = mu;
     out->sigma = sigma;
     out->loss_first = loss_first;
     out->loss_last = loss_last;
+    out->status = ok ? 0 : 1;
     // fold: w' = w / sigma, t = mu + sigma c, a = softmax(alpha)
     float amax = theta[0];
     for (int j = 1; j < kHidden; ++j) amax = fmaxf(amax, theta[j]);
@@ -276,6 +330,24 @@ learned_train_kernel(const float* __restrict__ xs, int64_t m, int steps, int bat
     }
     out->model.nbuckets = kLearnedBuckets;
   }
+}
+
+constexpr int kTrainThreads = 256;
+
+// Launches the training on one CTA per SM (cooperative launch: all CTAs are resident together,
+// which the grid barrier needs).  `sy` must point at device memory for one TrainSync.
+inline cudaError_t launch_learned_train(const float* xs, int64_t m, int steps, int batch, float lr, uint64_t seed,
+                                        TrainOut* out, TrainSync* sy, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sy, 0, sizeof(TrainSync), s);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, learned_train_kernel<kTrainThreads>, kTrainThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {(void*)&xs, (void*)&m, (void*)&steps, (void*)&batch, (void*)&lr, (void*)&seed, (void*)&out,
+                  (void*)&sy};
+  return cudaLaunchCooperativeKernel((const void*)learned_train_kernel<kTrainThreads>, dim3((unsigned)num_sms),
+                                     dim3(kTrainThreads), args, 0, s);
 }
 
 // Full-batch loss and gradient (sums over the finite points, normalised by their count) at a

@@ -41,15 +41,22 @@ int pdq_learned_train(const float* d_xs, int64_t m, int steps, int batch, float 
   if (m <= 0 || !d_xs || !d_ws || steps < 0 || batch <= 0) return set_error(PDQ_ERR_ARG, "bad argument");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   TrainOut* d_out = static_cast<TrainOut*>(d_ws);
+  TrainSync* d_sync = reinterpret_cast<TrainSync*>(static_cast<char*>(d_ws) + align_up(sizeof(TrainOut), 256));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  cudaError_t e;
   {
     LaunchScope ls("learned_train", s, 0.0);
-    learned_train_kernel<512><<<1, 512, 0, s>>>(d_xs, m, steps, batch, lr, 0x7A11ull, d_out);
+    e = launch_learned_train(d_xs, m, steps, batch, lr, 0x7A11ull, d_out, d_sync, sms, s);
   }
+  if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("learned_train: ") + cudaGetErrorString(e));
   TrainOut h;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_out, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, cudaGetErrorString(e));
+  if (h.status) return set_error(PDQ_ERR_TIMEOUT, "learned_train: a grid barrier gave up");
   if (h_theta) std::memcpy(h_theta, h.theta, sizeof(h.theta));
   if (h_norm_loss) {
     h_norm_loss[0] = h.mu;

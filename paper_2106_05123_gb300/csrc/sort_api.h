@@ -39,7 +39,7 @@ struct Layout {
   int64_t task_cap, round_cap, chunk_cap, item_cap, fb_cap;
   int64_t base_off[5];  // first entry of each base-sort size class's list (in items)
   int64_t base_cap[5];  // capacity of each class's list
-  size_t learned_xs, learned_out;  // learned path only
+  size_t learned_xs, learned_out, learned_sync;  // learned path only
   int64_t learned_m;
 };
 

@@ -20,8 +20,8 @@ inline int64_t chunk_min_for(int64_t n) {
   return c > 8192 ? c : 8192;
 }
 
-constexpr int kTrainSteps = 48;       // Adam steps of the learned model
-constexpr int kTrainBatch = 8192;     // points per step, drawn from the 1% sample
+constexpr int kTrainSteps = 24;       // Adam steps of the learned model
+constexpr int kTrainBatch = 32768;    // points per step, drawn from the 1% sample
 constexpr float kTrainLr = 0.05f;
 
 inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
@@ -68,6 +68,7 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
     L.learned_m = std::min<int64_t>(n, std::max<int64_t>(4096, n / 100));
     L.learned_xs = take((size_t)L.learned_m * sizeof(float));
     L.learned_out = take(sizeof(TrainOut));
+    L.learned_sync = take(sizeof(TrainSync));
   }
   L.total = off;
   return L;
@@ -262,7 +263,6 @@ class PlainSorter {
   // The learned level over the whole array (one task).
   int learned_round(int bad0, std::vector<Task>* nxt) {
     if constexpr (KT == PDQ_F32 && VB == 0) {
-      constexpr int kTrainThreads = 512;
       constexpr int kLTile = 4096;
       constexpr size_t kLScatterSmem = 2 * (size_t)kLTile * 4 + 3 * (size_t)kLearnedBuckets * 4 + (size_t)kLTile * 2;
       static bool configured = false;
@@ -296,12 +296,14 @@ class PlainSorter {
       }
       {
         LaunchScope ls("learned_train", st_, 0.0);
-        learned_train_kernel<kTrainThreads><<<1, kTrainThreads, 0, st_>>>(xs, m, kTrainSteps, kTrainBatch,
-                                                                         kTrainLr, seed ^ 0x7A11ull, tout);
+        TrainSync* sy = reinterpret_cast<TrainSync*>(ws + L_.learned_sync);
+        PDQ_CUDA(launch_learned_train(xs, m, kTrainSteps, kTrainBatch, kTrainLr, seed ^ 0x7A11ull, tout, sy,
+                                      a_.num_sms, st_));
       }
       PDQ_LAUNCHED("learned_train");
       PDQ_CUDA(cudaMemcpyAsync(&train_out_, tout, sizeof(TrainOut), cudaMemcpyDeviceToHost, st_));
       PDQ_CUDA(cudaStreamSynchronize(st_));
+      if (train_out_.status) return set_error(PDQ_ERR_TIMEOUT, "learned_train: a grid barrier gave up");
       const LearnedModel model = train_out_.model;
       // one task in about one large chunk per SM (keeps the 4096-bin scan short); chunks x 4096
       // bins must fit the count array
