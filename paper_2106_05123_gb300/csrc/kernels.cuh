@@ -598,6 +598,65 @@ scan_kernel(const int32_t* __restrict__ task_nbins, const int32_t* __restrict__ 
   }
 }
 
+// Chunk-parallel form of the scan for one task with many chunks (the first level): groups of
+// `per` consecutive chunks are summed per bin by separate CTAs (scan_group_sum_kernel), one CTA
+// turns the group sums into group bases and the task's bin starts (scan_group_base_kernel), and
+// the group CTAs then write every chunk's offsets (scan_group_apply_kernel).  `part` holds
+// groups x bin_stride words.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+scan_group_sum_kernel(const uint32_t* __restrict__ counts, int bin_stride, int nb, int nc, int per,
+                      uint32_t* __restrict__ part) {
+  const int g = blockIdx.x;
+  const int c0 = g * per, c1 = c0 + per < nc ? c0 + per : nc;
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    uint32_t s = 0;
+    for (int c = c0; c < c1; ++c) s += counts[(size_t)c * bin_stride + b];
+    part[(size_t)g * bin_stride + b] = s;
+  }
+}
+
+template <int THREADS, int MAXBINS>
+__global__ void __launch_bounds__(THREADS)
+scan_group_base_kernel(uint32_t* __restrict__ part, int bin_stride, int nb, int groups, uint2* __restrict__ children) {
+  __shared__ uint32_t tot[MAXBINS];
+  __shared__ uint32_t start[MAXBINS];
+  __shared__ uint32_t wtmp[THREADS / 32 + 1];
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    uint32_t run = 0;
+    for (int g = 0; g < groups; ++g) {
+      uint32_t* p = part + (size_t)g * bin_stride + b;
+      const uint32_t v = *p;
+      *p = run;  // exclusive prefix over the groups
+      run += v;
+    }
+    tot[b] = run;
+  }
+  __syncthreads();
+  block_exclusive_scan<THREADS>(tot, start, nb, wtmp);
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    for (int g = 0; g < groups; ++g) part[(size_t)g * bin_stride + b] += start[b];
+    children[b] = make_uint2(start[b], tot[b]);
+  }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+scan_group_apply_kernel(uint32_t* __restrict__ counts, int bin_stride, int nb, int nc, int per,
+                        const uint32_t* __restrict__ part) {
+  const int g = blockIdx.x;
+  const int c0 = g * per, c1 = c0 + per < nc ? c0 + per : nc;
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    uint32_t run = part[(size_t)g * bin_stride + b];
+    for (int c = c0; c < c1; ++c) {
+      uint32_t* p = counts + (size_t)c * bin_stride + b;
+      const uint32_t v = *p;
+      *p = run;
+      run += v;
+    }
+  }
+}
+
 // ================================================================== scatter
 // One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE elements,
 // double-buffered in shared memory by bulk copy (the last window's sub-16-byte tail is fetched
@@ -861,9 +920,10 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
 // 16 (8-byte codes), rounded up to a multiple of 4 so that each array that follows (positions,
 // values) starts 16-byte aligned.
 template <int KS>
-__host__ __device__ constexpr int base_sort_pcap(int cap) {
-  // + 32 slack elements: read-ahead one past a run and the padding of the last thread
-  return (cap + 32 + (cap + 32) / (KS == 4 ? 32 : 16) + 1 + 3) / 4 * 4;
+__host__ __device__ constexpr int base_sort_pcap(int cap, int items) {
+  // cap elements, one sentinel slot per run of the first merge round (runs of `items`), and
+  // 32 slack elements (read-ahead and the padding of the last thread); then the bank padding
+  return (cap + cap / items + 32 + (cap + cap / items + 32) / (KS == 4 ? 32 : 16) + 1 + 3) / 4 * 4;
 }
 
 template <class U>
@@ -922,7 +982,7 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   using V = typename Val<VB>::T;
   constexpr bool W = VB > 0;
   constexpr int CAP = THREADS * ITEMS;
-  constexpr int PCAP = base_sort_pcap<sizeof(U)>(CAP);
+  constexpr int PCAP = base_sort_pcap<sizeof(U)>(CAP, ITEMS);
   static_assert(PCAP % 4 == 0, "padded arrays must keep 16-byte alignment of the next array");
   U* sk = reinterpret_cast<U*>(smem);
   uint32_t* si = reinterpret_cast<uint32_t*>(sk + PCAP);
@@ -935,17 +995,23 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   const int P = na * ITEMS;
   const U* srck = (it.buf == kBufKeys ? keys : tmpk) + it.begin;
   const V* srcv = W ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
+  bool max_code = false;  // a real code equal to the sentinel value (all ones)
   for (int i = tid; i < P + ITEMS; i += THREADS) {  // ITEMS slack slots: harmless read-ahead
     U c = ~U(0);
     if (i < m) {
       const U x = srck[i];
       c = it.enc ? x : Key<KT>::enc(x);
+      max_code |= c == ~U(0);
       if (W) sv[i] = srcv[i];
     }
     sk[pad_idx<U>(i)] = c;
     if (W) si[pad_idx<U>(i)] = (uint32_t)i;
   }
-  __syncthreads();
+  // Keys only: a sentinel (all-ones code) ties with a real all-ones code, so a bucket holding
+  // one merges with bounds tests; with values the sentinel index (all ones) breaks every tie.
+  // (the block-wide OR is also the barrier after the staging writes: always executed)
+  const bool any_max = __syncthreads_or(max_code) != 0;
+  const bool checked = !W && any_max;
   U k[ITEMS];
   uint32_t x[ITEMS];
   const bool active = tid < na;
@@ -958,14 +1024,28 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
     }
     register_sort<W>(k, x);
   }
-  for (int R = ITEMS; R < P; R <<= 1) {
+  // Merge rounds.  Before round R the registers go back to shared memory with runs of R
+  // elements, each followed by one sentinel slot (all-ones code, all-ones index): run r starts at
+  // slot r * (R + 1).  A thread's ITEMS elements never straddle runs (ITEMS divides R).
+  int lg = 0;
+  while ((ITEMS << lg) < P) ++lg;
+  int R = ITEMS;
+  for (int round = 0; round < lg; ++round, R <<= 1) {
+    const int lgR = __ffs(R) - 1;
     __syncthreads();
     if (active) {
+      const int pos0 = tid * ITEMS;
+      const int slot0 = pos0 + (pos0 >> lgR);
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
-        const int p = pad_idx<U>(tid * ITEMS + e);
+        const int p = pad_idx<U>(slot0 + e);
         sk[p] = k[e];
         if (W) si[p] = x[e];
+      }
+      if (((pos0 + ITEMS) & (R - 1)) == 0 || pos0 + ITEMS == P) {  // last thread of its run
+        const int p = pad_idx<U>(slot0 + ITEMS);
+        sk[p] = ~U(0);
+        if (W) si[p] = 0xFFFFFFFFu;
       }
     }
     __syncthreads();
@@ -973,7 +1053,8 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
       const int pos = tid * ITEMS;
       const int g = pos & ~(2 * R - 1);  // first element of the pair of runs
       const int d = pos - g;             // this thread's diagonal inside the pair
-      const int a0 = g, b0 = g + R;
+      const int a0 = g + (g >> lgR);     // slot of run A's first element
+      const int b0 = a0 + R + 1;         // slot of run B's first element
       const int la = min(R, P - g);                  // run A (may be the ragged last run)
       const int lb = max(0, min(R, P - g - R));      // run B (may be short or empty)
       // merge-path split: the number of A elements among the first d outputs (ties take A)
@@ -987,26 +1068,54 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
           else hi = mid;
         }
       }
-      int ai = lo, bi = d - lo;
-      U ka = sk[pad_idx<U>(a0 + ai)], kb = sk[pad_idx<U>(b0 + bi)];
-      uint32_t xa = 0, xb = 0;
-      if (W) { xa = si[pad_idx<U>(a0 + ai)]; xb = si[pad_idx<U>(b0 + bi)]; }
-      // branch-free serial merge of ITEMS outputs: one shared load per output; a load one past
-      // the end of a run stays inside the array (slack) and is never selected
+      int ia = a0 + lo, ib = b0 + (d - lo);  // slots of the next A and B elements
+      U ka = lo < la ? sk[pad_idx<U>(ia)] : ~U(0), kb = d - lo < lb ? sk[pad_idx<U>(ib)] : ~U(0);
+      uint32_t xa = 0xFFFFFFFFu, xb = 0xFFFFFFFFu;
+      if (W) {
+        if (lo < la) xa = si[pad_idx<U>(ia)];
+        if (d - lo < lb) xb = si[pad_idx<U>(ib)];
+      }
+      if (!checked) {
+        // Sentinels end both runs, so an exhausted run is never chosen while the other still
+        // holds a smaller element.  Keys only: padding codes (all ones) tie with A's sentinel and
+        // ties take A, so A's index stops at its sentinel (those outputs are all-ones padding
+        // positions either way); with values the sentinel's all-ones index breaks every tie.
+        const int ea = a0 + la;
 #pragma unroll
-      for (int e = 0; e < ITEMS; ++e) {
-        const bool take_a = ai < la && (bi >= lb || !precedes<W>(kb, xb, ka, xa));
-        k[e] = take_a ? ka : kb;
-        x[e] = take_a ? xa : xb;
-        ai += take_a ? 1 : 0;
-        bi += take_a ? 0 : 1;
-        const int p = pad_idx<U>(take_a ? a0 + ai : b0 + bi);
-        const U nk = sk[p];
-        const uint32_t nx = W ? si[p] : 0u;
-        ka = take_a ? nk : ka;
-        kb = take_a ? kb : nk;
-        xa = take_a ? nx : xa;
-        xb = take_a ? xb : nx;
+        for (int e = 0; e < ITEMS; ++e) {
+          const bool take_a = !precedes<W>(kb, xb, ka, xa);
+          if (W) {
+            k[e] = take_a ? ka : kb;
+            x[e] = take_a ? xa : xb;
+            ia += take_a ? 1 : 0;
+          } else {
+            k[e] = ka < kb ? ka : kb;
+            ia = min(ia + (take_a ? 1 : 0), ea);
+          }
+          ib += take_a ? 0 : 1;
+          const int p = pad_idx<U>(take_a ? ia : ib);
+          const U nk = sk[p];
+          ka = take_a ? nk : ka;
+          kb = take_a ? kb : nk;
+          if (W) {
+            const uint32_t nx = si[p];
+            xa = take_a ? nx : xa;
+            xb = take_a ? xb : nx;
+          }
+        }
+      } else {
+        // keys only with a real all-ones code: the same merge with explicit run ends
+        const int ea = a0 + la, eb = b0 + lb;
+#pragma unroll
+        for (int e = 0; e < ITEMS; ++e) {
+          const bool take_a = ia < ea && (ib >= eb || !(kb < ka));
+          k[e] = take_a ? ka : kb;
+          ia += take_a ? 1 : 0;
+          ib += take_a ? 0 : 1;
+          const U nk = sk[pad_idx<U>(take_a ? ia : ib)];
+          ka = take_a ? nk : ka;
+          kb = take_a ? kb : nk;
+        }
       }
     }
   }
@@ -1042,7 +1151,7 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
 
 template <int KS, int VB, int THREADS, int ITEMS>
 constexpr size_t base_sort_smem() {
-  return (size_t)base_sort_pcap<KS>(THREADS * ITEMS) * (KS + (VB ? 4 : 0)) + (size_t)THREADS * ITEMS * VB;
+  return (size_t)base_sort_pcap<KS>(THREADS * ITEMS, ITEMS) * (KS + (VB ? 4 : 0)) + (size_t)THREADS * ITEMS * VB;
 }
 
 // ================================================================== copy temp -> keys (decode)

@@ -514,7 +514,19 @@ class PlainSorter {
     PDQ_LAUNCHED("count");
     {
       LaunchScope ls("scan", st_, 0.0);
-      scan_kernel<256, kBinsMax><<<nt, 256, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kBinsMax, children_);
+      constexpr int kPer = 8;  // chunks per group of the chunk-parallel scan
+      const int groups = (nchunks + kPer - 1) / kPer;
+      if (nt == 1 && nchunks >= 8 * kPer && (int64_t)nchunks + groups <= L_.chunk_cap) {
+        // one task with many chunks: the per-bin walk over all chunks would run on one CTA
+        uint32_t* part = counts_ + (size_t)nchunks * kBinsMax;  // rows past the used chunks
+        const int nb = meta[3 * nt];
+        scan_group_sum_kernel<256><<<groups, 256, 0, st_>>>(counts_, kBinsMax, nb, nchunks, kPer, part);
+        scan_group_base_kernel<512, kBinsMax><<<1, 512, 0, st_>>>(part, kBinsMax, nb, groups, children_);
+        scan_group_apply_kernel<256><<<groups, 256, 0, st_>>>(counts_, kBinsMax, nb, nchunks, kPer, part);
+        note_launch_count(2);
+      } else {
+        scan_kernel<256, kBinsMax><<<nt, 256, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kBinsMax, children_);
+      }
     }
     PDQ_LAUNCHED("scan");
     {
