@@ -261,6 +261,79 @@ def run_reference(args, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+E2_PATTERNS = ["uniform", "dupsq", "dup8", "mod8", "ones", "sort50", "sort90", "sort99", "organ", "merge",
+               "asc", "desc"]
+E2_LOG2N = [10, 13, 16, 19, 22, 24]
+
+
+def bench_e2_sweep(args) -> None:
+    """The paper's evaluation grid (Sec. 6.1 input distributions over a range of sizes), int32
+    keys, normalised like its figures: nanoseconds per (n log2 n).  The oracle is timed on the
+    host on the cells up to 2^16 keys for the same normalisation."""
+    import torch
+    import paper_2106_05123_gb300 as pdq
+    import oracle
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(pdq.pdq_workspace_bytes(1 << max(E2_LOG2N), pdq.PDQ_I32, 0), dtype=torch.uint8, device="cuda")
+    sweep, cpu_cells = {}, []
+    total_keys, total_ms = 0, 0.0
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    l0 = pdq.launch_count()
+    sampler.start()
+    for pat in E2_PATTERNS:
+        sweep[pat] = {}
+        for lg in E2_LOG2N:
+            n = 1 << lg
+            a = workloads.pattern(pat, n, workloads.config_seed(5), dtype=np.int32)
+            src = torch.from_numpy(a).cuda()
+            work = torch.empty_like(src)
+            times = []
+            for it in range(args.warmup + min(args.steps, 5)):
+                work.copy_(src)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                pdq.pdq_sort_keys(work, ws, key_dtype=pdq.PDQ_I32)
+                e1.record()
+                torch.cuda.synchronize()
+                if it >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+            if pat in ("uniform", "dupsq"):
+                assert bool((work[1:] >= work[:-1]).all().item()), "output not sorted"
+            ms = float(statistics.median(times))
+            total_keys += n * len(times)
+            total_ms += sum(times)
+            cell = {"gpu_ns_per_nlogn": ms * 1e6 / (n * lg), "gpu_ms": ms}
+            if lg <= 16:
+                reps = max(1, (1 << 18) // n)
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    b = a.copy()
+                    oracle.pdqsort(b)
+                dt = (time.perf_counter() - t0) / reps
+                cell["cpu_ns_per_nlogn"] = dt * 1e9 / (n * lg)
+                cpu_cells.append((n, dt))
+            sweep[pat][f"2^{lg}"] = cell
+    clocks = sampler.stop()
+    launches = pdq.launch_count() - l0
+    cpu_keys = sum(n for n, _ in cpu_cells)
+    cpu_s = sum(t for _, t in cpu_cells)
+    line = {"metric": "Gkeys/s", "value": total_keys / (total_ms * 1e-3) / 1e9, "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": min(args.steps, 5), "warmup": args.warmup, "ms_per_step": total_ms / max(1, min(args.steps, 5)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "e2_sweep", "description": "Sec. 6.1 input distributions x sizes, int32",
+                       "patterns": E2_PATTERNS, "log2_n": E2_LOG2N,
+                       "l2": "flushed (512 MiB write) and input restored between sorts"},
+            "sweep": sweep, "roofline": None,
+            "cpu_baseline": {"value": cpu_keys / cpu_s / 1e9 if cpu_s else None, "unit": "Gkeys/s", "cores": 1,
+                             "kind": "oracle", "sample": "every pattern at 2^10, 2^13, 2^16 keys"},
+            "e2e": None, "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def dtype_name(name: str) -> str:
     _, _, kdt, vdt = WORKLOADS[name]
     s = {np.int32: "int32", np.int64: "int64", np.uint64: "uint64", np.float32: "f32"}[kdt]
@@ -273,13 +346,23 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="uniform_i32_2p28", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="uniform_i32_2p28", choices=sorted(WORKLOADS) + ["e2_sweep"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "e2_sweep":
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the e2 sweep times the oracle "
+                                  "inside its own line (cpu_ns_per_nlogn per cell)"}), flush=True)
+            return
+        if rank != 0:
+            return
+        bench_e2_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return
