@@ -471,7 +471,13 @@ class PlainSorter {
     const int64_t n = a_.n;
     int64_t total = 0;
     for (int i = 0; i < nt; ++i) total += tasks[i].size;
-    int64_t ch = std::max<int64_t>(chunk_min_for(n), (total + a_.num_sms * 4 - 1) / (a_.num_sms * 4));
+    // Chunks: one task is cut into one chunk per resident count CTA (4 per SM, one wave; the
+    // scatter runs two per SM, two waves).  Several tasks cannot share chunks, so each task is
+    // cut into equal parts of at most about total / (2 waves) elements: two near-full waves
+    // instead of one full wave and a ragged tail.
+    const int64_t slots = (int64_t)a_.num_sms * 4;
+    const int64_t want = nt == 1 ? slots : 2 * slots;
+    const int64_t ch = std::max<int64_t>(chunk_min_for(n), (total + want - 1) / want);
     std::vector<int32_t> meta(4 * (size_t)nt);
     std::vector<Chunk> chunks;
     chunks.reserve((size_t)(total / ch + nt + 1));
@@ -481,10 +487,13 @@ class PlainSorter {
       max_logb = std::max(max_logb, lb);
       meta[i] = lb;
       meta[nt + i] = (int32_t)chunks.size();
-      int32_t nc = 0;
-      for (int64_t o = 0; o < tasks[i].size; o += ch, ++nc)
-        chunks.push_back(Chunk{tasks[i].begin + o, (int32_t)std::min<int64_t>(ch, tasks[i].size - o), i});
-      meta[2 * nt + i] = nc;
+      const int64_t size = tasks[i].size;
+      const int64_t parts = std::max<int64_t>(1, (size + ch - 1) / ch);
+      for (int64_t j = 0; j < parts; ++j) {
+        const int64_t o0 = size * j / parts, o1 = size * (j + 1) / parts;
+        chunks.push_back(Chunk{tasks[i].begin + o0, (int32_t)(o1 - o0), i});
+      }
+      meta[2 * nt + i] = (int32_t)parts;
       meta[3 * nt + i] = 2 << lb;
     }
     const int nchunks = (int)chunks.size();
