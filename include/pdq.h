@@ -71,6 +71,8 @@ typedef struct {
   int64_t bad_splits;        /* children that kept more than 7/8 of their parent (Sec. 4.1) */
   int64_t base_buckets;      /* buckets finished by the shared-memory base sort (Sec. 5.1) */
   int64_t kernel_launches;   /* kernels launched by the call */
+  int64_t fixup_peeled;      /* nearly-sorted fix-up: keys peeled off descents and merged back
+                                (0 when the fix-up did not run) */
 } pdq_stats;
 
 /* Tuning knobs.  Zero in a field means "library default".  Used by tests to force rare paths
@@ -85,6 +87,8 @@ typedef struct {
   int32_t inject_wait;      /* test hook, segmented path: one CTA first waits on a flag nothing
                                sets; with a short wait_limit_us the call returns PDQ_ERR_TIMEOUT */
   int32_t seg_block;        /* segmented path: persistent kernel block size, 256 or 512 (default) */
+  int32_t fixup;            /* 1: try the nearly-sorted fix-up when the probe finds few descents
+                               (peel the keys of every descent, sort them, merge; default 0: off) */
 } pdq_tuning;
 
 /* Bytes of workspace the sort of n keys (and a payload of value_bytes, 0 for keys only) needs.

@@ -44,7 +44,7 @@ class PdqError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "passes", "equal_buckets", "fallback_buckets", "reversed", "sorted_exit",
-        "learned_overflow", "bad_splits", "base_buckets", "kernel_launches")]
+        "learned_overflow", "bad_splits", "base_buckets", "kernel_launches", "fixup_peeled")]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
@@ -54,7 +54,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("log2_buckets", ctypes.c_int32), ("oversample", ctypes.c_int32),
                 ("base_capacity", ctypes.c_int32), ("bad_allowed", ctypes.c_int32),
                 ("probe", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32),
-                ("inject_wait", ctypes.c_int32), ("seg_block", ctypes.c_int32)]
+                ("inject_wait", ctypes.c_int32), ("seg_block", ctypes.c_int32), ("fixup", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -218,6 +218,11 @@ struct alignas(2 * sizeof(U)) PrefEnt {
   U range;
   U s0;
 };
+// Bytes of one task's prefilter table, the same for both key widths.
+constexpr size_t kPrefTableBytes = 16384;
+static_assert(pref_entries<uint32_t>() * sizeof(PrefEnt<uint32_t>) == kPrefTableBytes &&
+                  pref_entries<uint64_t>() * sizeof(PrefEnt<uint64_t>) == kPrefTableBytes,
+              "prefilter table size");
 
 template <class U>
 struct Pref {
@@ -1165,6 +1170,176 @@ __global__ void copy_kernel(const Item* __restrict__ items, typename Key<KT>::U*
     const int64_t p = it.begin + i;
     keys[p] = Key<KT>::dec(tmpk[p]);
     if (VB) vals[p] = tmpv[p];
+  }
+}
+
+// ================================================================== nearly-sorted fix-up
+// For input with few descents (Sec. 5.2's partial insertion sort has the same aim: finish an
+// almost sorted range in linear time).  Both elements of every descent are peeled off into a
+// side array E until the remainder R has no descent; E is sorted on its own, and R and E are
+// merged.  Element i of src[0..len) is peeled when src[i-1] > src[i] or src[i] > src[i+1]
+// (order of the encoded codes).
+template <int KT>
+__device__ __forceinline__ bool fix_peeled(const typename Key<KT>::U* __restrict__ src, int64_t len, int64_t i) {
+  using U = typename Key<KT>::U;
+  const U x = Key<KT>::enc(src[i]);
+  const bool left = i > 0 && Key<KT>::enc(src[i - 1]) > x;
+  const bool right = i + 1 < len && x > Key<KT>::enc(src[i + 1]);
+  return left || right;
+}
+
+// Peeled elements per tile of TILE elements.
+template <int KT, int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS)
+fix_count_kernel(const typename Key<KT>::U* __restrict__ src, int64_t len, uint32_t* __restrict__ tile_cnt) {
+  __shared__ uint32_t wsum[THREADS / 32];
+  const int64_t t0 = (int64_t)blockIdx.x * TILE;
+  uint32_t c = 0;
+  for (int j = threadIdx.x; j < TILE; j += THREADS) {
+    const int64_t i = t0 + j;
+    if (i < len) c += fix_peeled<KT>(src, len, i) ? 1u : 0u;
+  }
+  c = warp_sum(c);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < THREADS / 32; ++w) t += wsum[w];
+    tile_cnt[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the tile counts in place (one CTA); *total receives the sum.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+fix_scan_kernel(uint32_t* __restrict__ tile_cnt, int ntiles, unsigned long long* __restrict__ total) {
+  __shared__ uint32_t wtmp[THREADS / 32 + 1];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += THREADS) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < ntiles ? tile_cnt[i] : 0u;
+    // inclusive warp scan, then across warps
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wtmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < THREADS / 32 ? wtmp[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < THREADS / 32) wtmp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = carry + (warp ? wtmp[warp - 1] : 0u) + x - v;
+    if (i < ntiles) tile_cnt[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == THREADS - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Kept elements go to dst (in order), peeled ones to pe[e_off + ...] (in order).  Warp w of a
+// tile owns the 32 * PER consecutive elements from t0 + w * 32 * PER; row e of the warp is the
+// 32 consecutive elements base + 32 e + lane (coalesced), ranked by ballots.
+template <int KT, int VB, int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS)
+fix_compact_kernel(const typename Key<KT>::U* __restrict__ src, const typename Val<VB>::T* __restrict__ srcv,
+                   int64_t len, typename Key<KT>::U* __restrict__ dst, typename Val<VB>::T* __restrict__ dstv,
+                   typename Key<KT>::U* __restrict__ pe, typename Val<VB>::T* __restrict__ pev, int64_t e_off,
+                   const uint32_t* __restrict__ tile_pre) {
+  constexpr int NW = THREADS / 32;
+  constexpr int PER = TILE / THREADS;  // rows per warp
+  static_assert(TILE % THREADS == 0 && PER <= 32, "tile shape");
+  __shared__ uint32_t wcnt[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t base = (int64_t)blockIdx.x * TILE + (int64_t)warp * 32 * PER;
+  uint32_t mask[PER];
+  uint32_t peeled = 0;
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    const int64_t i = base + 32 * e + lane;
+    mask[e] = __ballot_sync(0xffffffffu, i < len && fix_peeled<KT>(src, len, i));
+    peeled += (uint32_t)__popc(mask[e]);
+  }
+  if (lane == 0) wcnt[warp] = peeled;
+  __syncthreads();
+  uint32_t before = tile_pre[blockIdx.x];  // peeled elements before this warp's range
+  for (int w = 0; w < warp; ++w) before += wcnt[w];
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int e = 0; e < PER; ++e) {
+    const int64_t i = base + 32 * e + lane;
+    const uint32_t p = before + (uint32_t)__popc(mask[e] & lt);  // peeled before element i
+    if (i < len) {
+      if ((mask[e] >> lane) & 1u) {
+        pe[e_off + p] = src[i];
+        if (VB) pev[e_off + p] = srcv[i];
+      } else {
+        dst[i - p] = src[i];
+        if (VB) dstv[i - p] = srcv[i];
+      }
+    }
+    before += (uint32_t)__popc(mask[e]);
+  }
+}
+
+// Merge of two ascending arrays (raw keys, compared by their codes) into out[0..la+lb): each
+// thread finds its merge-path split for ITEMS outputs by binary search, merges them into shared
+// memory, and the block writes its THREADS * ITEMS outputs with coalesced stores.  Ties take A.
+template <int KT, int VB, int THREADS, int ITEMS>
+__global__ void __launch_bounds__(THREADS)
+fix_merge_kernel(const typename Key<KT>::U* __restrict__ A, const typename Val<VB>::T* __restrict__ Av, int64_t la,
+                 const typename Key<KT>::U* __restrict__ B, const typename Val<VB>::T* __restrict__ Bv, int64_t lb,
+                 typename Key<KT>::U* __restrict__ out, typename Val<VB>::T* __restrict__ outv) {
+  using U = typename Key<KT>::U;
+  using V = typename Val<VB>::T;
+  constexpr int BLK = THREADS * ITEMS;
+  __shared__ U sk[BLK];
+  __shared__ V sv[VB ? BLK : 1];
+  const int64_t total = la + lb;
+  const int64_t b0 = (int64_t)blockIdx.x * BLK;
+  const int64_t d = b0 + (int64_t)threadIdx.x * ITEMS;
+  if (d < total) {
+    int64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (!(Key<KT>::enc(B[d - 1 - mid]) < Key<KT>::enc(A[mid]))) lo = mid + 1;
+      else hi = mid;
+    }
+    int64_t ia = lo, ib = d - lo;
+    const int cnt = (int)(total - d < ITEMS ? total - d : ITEMS);
+    for (int e = 0; e < cnt; ++e) {
+      const bool take_a = ia < la && (ib >= lb || !(Key<KT>::enc(B[ib]) < Key<KT>::enc(A[ia])));
+      const int s = threadIdx.x * ITEMS + e;
+      if (take_a) {
+        sk[s] = A[ia];
+        if (VB) sv[s] = Av[ia];
+        ++ia;
+      } else {
+        sk[s] = B[ib];
+        if (VB) sv[s] = Bv[ib];
+        ++ib;
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < BLK; j += THREADS) {
+    const int64_t o = b0 + j;
+    if (o < total) {
+      out[o] = sk[j];
+      if (VB) outv[o] = sv[j];
+    }
   }
 }
 

@@ -19,6 +19,7 @@ struct Tuning {
   int wait_us;       // bound of the persistent kernel's waits (0: 2 s)
   int inject_wait;   // test hook: the persistent kernel first waits on a flag nobody sets
   int seg_block;     // persistent kernel block size (256 or 512)
+  bool fixup;        // try the nearly-sorted fix-up
 };
 
 struct SortArgs {
@@ -41,6 +42,10 @@ struct Layout {
   int64_t base_cap[5];  // capacity of each class's list
   size_t learned_xs, learned_out, learned_sync;  // learned path only
   int64_t learned_m;
+  // nearly-sorted fix-up (absent in nested sorts and below kFixMin elements): peeled keys and
+  // values (up to fix_m), per-tile counts, and the workspace of the peeled keys' own sort
+  size_t fix_e, fix_ev, fix_cnt, fix_ws, fix_ws_bytes;
+  int64_t fix_m;
 };
 
 // Arguments of the segmented sort.

@@ -24,7 +24,10 @@ constexpr int kTrainSteps = 24;       // Adam steps of the learned model
 constexpr int kTrainBatch = 32768;    // points per step, drawn from the 1% sample
 constexpr float kTrainLr = 0.05f;
 
-inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
+constexpr int64_t kFixMin = int64_t(1) << 16;  // smallest array given the nearly-sorted fix-up
+constexpr int kFixTile = 8192;                 // elements per tile of the fix-up's peel pass
+
+inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool fixup = true) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
   const int64_t cmin = kBaseCapMin;
@@ -60,7 +63,7 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
   L.spl = take((size_t)L.round_cap * kBMax * ks);
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
   L.pref = take((size_t)L.round_cap * 32);
-  L.tab = take((size_t)L.round_cap * kPrefEntriesMax * 16);
+  L.tab = take((size_t)L.round_cap * kPrefTableBytes);
   L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
@@ -69,6 +72,14 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false) {
     L.learned_xs = take((size_t)L.learned_m * sizeof(float));
     L.learned_out = take(sizeof(TrainOut));
     L.learned_sync = take(sizeof(TrainSync));
+  }
+  if (fixup && n >= kFixMin) {
+    L.fix_m = n / 16;
+    L.fix_e = take((size_t)(L.fix_m + 16) * ks);
+    L.fix_ev = take((size_t)(L.fix_m + 16) * vb);
+    L.fix_cnt = take((size_t)(n / kFixTile + 2) * sizeof(uint32_t));
+    L.fix_ws_bytes = make_layout(L.fix_m, ks, vb, false, false).total;
+    L.fix_ws = take(L.fix_ws_bytes);
   }
   L.total = off;
   return L;
@@ -123,9 +134,9 @@ class PlainSorter {
   using S = Shape<KS, VB>;
 
  public:
-  explicit PlainSorter(const SortArgs& a, bool learned = false) : a_(a) {
+  explicit PlainSorter(const SortArgs& a, bool learned = false, bool nested = false) : a_(a) {
     cap_ = std::min(a.tune.base_cap, S::kMaxCap);
-    L_ = make_layout(a.n, KS, VB, learned);
+    L_ = make_layout(a.n, KS, VB, learned, !nested);
     char* ws = static_cast<char*>(a.ws);
     // The tile kernels need 16-byte-aligned buffers: a key array that starts off a 16-byte
     // boundary is addressed from the boundary below it, and every index is shifted by off_
@@ -230,9 +241,14 @@ class PlainSorter {
       return base_sort(cls, 1, kBufKeys, 1, n);
     }
     if (a_.tune.probe) {
-      bool sorted = false;
-      rc = probe(&sorted);
+      bool sorted = false, nearly = false;
+      rc = probe(&sorted, &nearly);
       if (rc || sorted) return rc;
+      if (nearly) {
+        bool fixed = false;
+        rc = fixup(&fixed);
+        if (rc || fixed) return rc;
+      }
     }
     const int bad0 = a_.tune.bad_allowed > 0 ? a_.tune.bad_allowed
                                               : (a_.tune.bad_allowed < 0 ? 0 : ilog2_floor((uint64_t)n));
@@ -396,8 +412,9 @@ class PlainSorter {
 
   // Sorted / reverse probe (Sec. 5.2): a sample first, the full pass only when the sample is
   // monotone.  Sets *done when the array needs nothing more.
-  int probe(bool* done) {
+  int probe(bool* done, bool* nearly) {
     const int64_t n = a_.n;
+    const bool can_fix = a_.tune.fixup && L_.fix_m > 0;
     unsigned long long h[4];
     auto run_probe = [&](int64_t stride) -> int {
       const unsigned long long init[4] = {0, 0, ~0ull, 0};
@@ -418,7 +435,9 @@ class PlainSorter {
     const int64_t stride = std::max<int64_t>(1, n / 65536);
     int rc = run_probe(stride);
     if (rc) return rc;
-    if (stride > 1 && h[0] != 0 && h[1] != 0) return PDQ_OK;  // sample is neither monotone
+    const int64_t m_sample = (n - 1) / stride + 1;
+    // the sample is neither monotone: unless its descents are few (nearly ascending), sort
+    if (stride > 1 && h[0] != 0 && h[1] != 0 && !(can_fix && (int64_t)h[0] * 16 <= m_sample)) return PDQ_OK;
     if (stride > 1) {
       rc = run_probe(1);
       if (rc) return rc;
@@ -442,6 +461,105 @@ class PlainSorter {
       PDQ_LAUNCHED("reverse");
       return PDQ_OK;
     }
+    if (can_fix && (int64_t)h[0] <= n / 32) *nearly = true;  // few descents: the fix-up
+    return PDQ_OK;
+  }
+
+  // Nearly-sorted fix-up: peel both elements of every descent into E (at most fix_m, at most
+  // six rounds, each at most half the previous) until the remainder R has no descent, sort E on its own, merge R and E into the
+  // key buffer.  *fixed is false when the bounds are hit: the arrays then hold R followed by E
+  // (a permutation of the input) and the caller sorts them the ordinary way.
+  int fixup(bool* fixed) {
+    *fixed = false;
+    const int64_t n = a_.n;
+    char* ws = static_cast<char*>(a_.ws);
+    U* E = reinterpret_cast<U*>(ws + L_.fix_e);
+    V* Ev = reinterpret_cast<V*>(ws + L_.fix_ev);
+    uint32_t* tc = reinterpret_cast<uint32_t*>(ws + L_.fix_cnt);
+    U* cur = keys_ + off_;
+    V* curv = VB ? vals_ + off_ : nullptr;
+    U* oth = tmpk_ + off_;
+    V* othv = VB ? tmpv_ + off_ : nullptr;
+    int64_t len = n, e_len = 0;
+    bool clean = false, over = false;
+    unsigned long long r_prev = 0;
+    for (int round = 0; round < 6; ++round) {
+      const int ntiles = (int)((len + kFixTile - 1) / kFixTile);
+      {
+        LaunchScope ls("fixup_peel", st_, (double)len * KS);
+        fix_count_kernel<KT, 256, kFixTile><<<ntiles, 256, 0, st_>>>(cur, len, tc);
+        fix_scan_kernel<1024><<<1, 1024, 0, st_>>>(tc, ntiles, &ctr_->probe[4]);
+        note_launch_count(1);
+      }
+      PDQ_LAUNCHED("fixup_peel");
+      unsigned long long r = 0;
+      PDQ_CUDA(cudaMemcpyAsync(&r, &ctr_->probe[4], sizeof(r), cudaMemcpyDeviceToHost, st_));
+      PDQ_CUDA(cudaStreamSynchronize(st_));
+      if (r == 0) {
+        clean = true;
+        break;
+      }
+      // give up past the side array's capacity, or when a round does not at least halve the
+      // previous one (long ascending runs: peeling only moves their boundaries)
+      if (e_len + (int64_t)r > L_.fix_m || (round > 0 && 2 * r > r_prev)) {
+        over = true;
+        break;
+      }
+      r_prev = r;
+      {
+        LaunchScope ls("fixup_compact", st_, 2.0 * (double)len * (KS + VB));
+        fix_compact_kernel<KT, VB, 256, kFixTile><<<ntiles, 256, 0, st_>>>(cur, curv, len, oth, othv, E, Ev, e_len, tc);
+      }
+      PDQ_LAUNCHED("fixup_compact");
+      e_len += (int64_t)r;
+      len -= (int64_t)r;
+      std::swap(cur, oth);
+      std::swap(curv, othv);
+    }
+    const bool in_keys = cur == keys_ + off_;
+    if (!clean || over) {
+      // give up: the key buffer gets R then E, a permutation of the input
+      if (!in_keys) {
+        PDQ_CUDA(cudaMemcpyAsync(keys_ + off_, cur, (size_t)len * KS, cudaMemcpyDeviceToDevice, st_));
+        if (VB) PDQ_CUDA(cudaMemcpyAsync(vals_ + off_, curv, (size_t)len * VB, cudaMemcpyDeviceToDevice, st_));
+      }
+      if (e_len) {
+        PDQ_CUDA(cudaMemcpyAsync(keys_ + off_ + len, E, (size_t)e_len * KS, cudaMemcpyDeviceToDevice, st_));
+        if (VB) PDQ_CUDA(cudaMemcpyAsync(vals_ + off_ + len, Ev, (size_t)e_len * VB, cudaMemcpyDeviceToDevice, st_));
+      }
+      return PDQ_OK;
+    }
+    stats_.fixup_peeled = e_len;
+    if (e_len > 1) {  // the peeled keys' own sort (no fix-up inside it)
+      SortArgs sa = a_;
+      sa.keys = E;
+      sa.vals = VB ? static_cast<void*>(Ev) : nullptr;
+      sa.n = e_len;
+      sa.ws = ws + L_.fix_ws;
+      sa.ws_bytes = L_.fix_ws_bytes;
+      PlainSorter<KT, VB> sub(sa, false, true);
+      const int rc = sub.run();
+      if (rc) return rc;
+      stats_.passes = sub.stats_.passes;
+      stats_.base_buckets += sub.stats_.base_buckets;
+      stats_.equal_buckets += sub.stats_.equal_buckets;
+      stats_.fallback_buckets += sub.stats_.fallback_buckets;
+    }
+    if (in_keys) {  // the merge writes the key buffer, so R moves out of it first
+      PDQ_CUDA(cudaMemcpyAsync(tmpk_ + off_, cur, (size_t)len * KS, cudaMemcpyDeviceToDevice, st_));
+      if (VB) PDQ_CUDA(cudaMemcpyAsync(tmpv_ + off_, curv, (size_t)len * VB, cudaMemcpyDeviceToDevice, st_));
+      cur = tmpk_ + off_;
+      curv = VB ? tmpv_ + off_ : nullptr;
+    }
+    {
+      constexpr int kMT = 256, kMI = 8;
+      const int64_t blocks = (n + kMT * kMI - 1) / (kMT * kMI);
+      LaunchScope ls("fixup_merge", st_, 2.0 * (double)n * (KS + VB));
+      fix_merge_kernel<KT, VB, kMT, kMI><<<(unsigned)blocks, kMT, 0, st_>>>(cur, curv, len, E, Ev, e_len,
+                                                                           keys_ + off_, VB ? vals_ + off_ : nullptr);
+    }
+    PDQ_LAUNCHED("fixup_merge");
+    *fixed = true;
     return PDQ_OK;
   }
 

@@ -191,3 +191,58 @@ def test_misaligned_subarrays(dtype, lo, hi):
         gk, gv = to_host(dk, dtype), to_host(dv, v.dtype).astype(np.int64)
         assert np.array_equal(bits(gk), bits(want))
         assert np.array_equal(a[gv], gk) and np.array_equal(gv[:lo], np.arange(lo))
+
+
+# ---------------------------------------------------------------- nearly-sorted fix-up
+FIXUP = {"fixup": 1}
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint32, np.int64, np.uint64, np.float32])
+@pytest.mark.parametrize("n", [1 << 16, (1 << 20) + 17, 3_000_001])
+def test_nearly_sorted_fixup_exact(dtype, n):
+    """Ascending with 1% random transpositions: the probe sees few descents, the fix-up peels,
+    sorts and merges them; the keys match the oracle."""
+    a = workloads.pattern("asc_swaps", n, workloads.config_seed(80), dtype=np.int64)
+    a = (a - n // 2).astype(dtype) if dtype in (np.int32, np.int64, np.float32) else a.astype(dtype)
+    got, _, st = gpu_sort(a, tuning=FIXUP)
+    want = a.copy()
+    oracle.pdqsort(want)
+    assert np.array_equal(bits(got), bits(want))
+    assert st["fixup_peeled"] > 0
+    _, _, st_off = gpu_sort(a)  # off by default
+    assert st_off["fixup_peeled"] == 0
+
+
+@pytest.mark.parametrize("name", ["sort99", "merge", "sawtooth", "asc_swaps"])
+def test_nearly_sorted_patterns_pairs(name):
+    """Pairs through the fix-up (or through its give-up path back to the ordinary sort)."""
+    n = (1 << 20) + 3
+    k = workloads.pattern(name, n, workloads.config_seed(81), dtype=np.int32)
+    v = np.arange(n, dtype=np.uint32)
+    ko, vo, st = gpu_sort(k, v, tuning=FIXUP)
+    want = k.copy()
+    oracle.pdqsort(want)
+    assert np.array_equal(ko, want)
+    assert np.array_equal(k[vo.astype(np.int64)], ko)
+    if name == "asc_swaps":
+        assert st["fixup_peeled"] > 0
+    elif name in ("merge", "sawtooth"):  # long runs: peeling does not converge, the sort takes over
+        assert st["fixup_peeled"] == 0
+
+
+@pytest.mark.parametrize("kind", ["reversed_triples", "rotated_blocks"])
+def test_nearly_sorted_clustered_displacements(kind):
+    """Displaced blocks every 40 elements: reversed triples peel in one round; rotated blocks of
+    six need one round per pair and make the fix-up give up.  Either way the keys are exact."""
+    n = 1 << 20
+    a = np.arange(n, dtype=np.int64)
+    for s0 in range(7, n - 8, 40):
+        if kind == "reversed_triples":
+            a[s0:s0 + 3] = a[s0:s0 + 3][::-1].copy()
+        else:
+            a[s0:s0 + 6] = np.concatenate([a[s0 + 3:s0 + 6], a[s0:s0 + 3]])
+    a = a.astype(np.int32)
+    got, _, st = gpu_sort(a, tuning=FIXUP)
+    assert np.array_equal(got, np.sort(a))
+    want = a.copy()
+    oracle.pdqsort(want)
+    assert np.array_equal(got, want)
