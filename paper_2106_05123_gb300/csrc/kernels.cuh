@@ -1030,17 +1030,33 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
     register_sort<W>(k, x);
   }
   // Merge rounds.  Before round R the registers go back to shared memory with runs of R
-  // elements, each followed by one sentinel slot (all-ones code, all-ones index): run r starts at
-  // slot r * (R + 1).  A thread's ITEMS elements never straddle runs (ITEMS divides R).
+  // elements, each followed by one sentinel slot (all-ones code, all-ones index).  While a pair of
+  // runs (2R elements) lies inside one warp's WSPAN = 32 * ITEMS elements, each warp keeps a fixed
+  // region of WSPAN + 32 slots (its runs and their sentinels), so the round reads only what its
+  // own warp wrote and a warp barrier suffices; wider rounds use one array-wide layout (run r at
+  // slot r * (R + 1)) and block barriers.  A thread's ITEMS elements never straddle runs.
+  constexpr int WSPAN = 32 * ITEMS;
+  constexpr int WSTRIDE = WSPAN + 32;
+  constexpr int LG_WSPAN = ITEMS == 32 ? 10 : (ITEMS == 16 ? 9 : 8);
+  static_assert((1 << LG_WSPAN) == WSPAN, "ITEMS must be 8, 16 or 32");
+  auto slot_of = [&](int pos, int lgR, bool wl) {
+    if (wl) {
+      const int lp = pos & (WSPAN - 1);
+      return (pos >> LG_WSPAN) * WSTRIDE + lp + (lp >> lgR);
+    }
+    return pos + (pos >> lgR);
+  };
   int lg = 0;
   while ((ITEMS << lg) < P) ++lg;
   int R = ITEMS;
   for (int round = 0; round < lg; ++round, R <<= 1) {
     const int lgR = __ffs(R) - 1;
-    __syncthreads();
+    const bool warp_local = 2 * R <= WSPAN;
+    // the first round's layout differs from the staging layout across warps: block barrier
+    if (warp_local && round > 0) __syncwarp(); else __syncthreads();
     if (active) {
       const int pos0 = tid * ITEMS;
-      const int slot0 = pos0 + (pos0 >> lgR);
+      const int slot0 = slot_of(pos0, lgR, warp_local);
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
         const int p = pad_idx<U>(slot0 + e);
@@ -1053,13 +1069,13 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
         if (W) si[p] = 0xFFFFFFFFu;
       }
     }
-    __syncthreads();
+    if (warp_local) __syncwarp(); else __syncthreads();
     if (active) {
       const int pos = tid * ITEMS;
-      const int g = pos & ~(2 * R - 1);  // first element of the pair of runs
-      const int d = pos - g;             // this thread's diagonal inside the pair
-      const int a0 = g + (g >> lgR);     // slot of run A's first element
-      const int b0 = a0 + R + 1;         // slot of run B's first element
+      const int g = pos & ~(2 * R - 1);             // first element of the pair of runs
+      const int d = pos - g;                        // this thread's diagonal inside the pair
+      const int a0 = slot_of(g, lgR, warp_local);   // slot of run A's first element
+      const int b0 = a0 + R + 1;                    // slot of run B's first element
       const int la = min(R, P - g);                  // run A (may be the ragged last run)
       const int lb = max(0, min(R, P - g - R));      // run B (may be short or empty)
       // merge-path split: the number of A elements among the first d outputs (ties take A)

@@ -14,8 +14,8 @@
 // result is exact whatever the model's quality; quality only changes bucket balance.
 //
 // Training: on a sorted sample xs[0..m) the target of xs[i] is its empirical CDF (i + 0.5) / m;
-// the loss is the mean squared error, minimised with Adam by one CTA over minibatches drawn
-// from the whole sample, with the hand-written gradient below.  Adam moves each ramp start in
+// the loss is the mean squared error, minimised with Adam over minibatches drawn from the whole
+// sample, with the hand-written gradient below, by one cooperative launch of one CTA per SM.  Adam moves each ramp start in
 // units of that ramp's initial width (c_j = c0_j + s_j d_j, d_j trained), so a step shifts a
 // narrow ramp by a fraction of its own width rather than of the whole key range.
 #pragma once
