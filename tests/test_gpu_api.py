@@ -1,0 +1,98 @@
+"""The remaining C-ABI calls on the GPU: the host-buffer sort, in-place reversal, sorting on a
+caller stream, workspace errors, and the library's own launch counting and per-kernel timing."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2106_05123_gb300 as pdq
+import workloads
+from gpu_helpers import CODE, bits, to_device, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint64, np.float32])
+def test_sort_host_matches_oracle(dtype):
+    n = 777_777
+    a = workloads.uniform_bits(n, dtype, workloads.config_seed(90)) if dtype != np.float32 else \
+        workloads.normal_f32_specials(n, workloads.config_seed(90))[0]
+    h = torch.from_numpy(a.copy() if dtype == np.float32 else
+                         a.view({4: np.int32, 8: np.int64}[a.dtype.itemsize]).copy()).pin_memory()
+    d = torch.empty(n, dtype=h.dtype, device="cuda")
+    ws = pdq.workspace_for(n, CODE[a.dtype])
+    # the binding infers the code from the tensor dtype; unsigned keys need the explicit code
+    st = pdq.Stats()
+    rc = pdq.lib().pdq_sort_host(h.data_ptr(), None, 0, n, CODE[a.dtype], d.data_ptr(), None, ws.data_ptr(),
+                                 ws.numel(), None, None, pdq.ctypes.byref(st))
+    assert rc == 0, pdq.lib().pdq_last_error()
+    got = h.numpy().view(a.dtype)
+    want = a.copy()
+    oracle.pdqsort(want)
+    assert np.array_equal(bits(got), bits(want))
+
+
+def test_sort_host_pairs():
+    n = 300_001
+    k = workloads.uniform_bits(n, np.int32, workloads.config_seed(91)) % 5000
+    hk = torch.from_numpy(k.copy()).pin_memory()
+    hv = torch.arange(n, dtype=torch.int32).pin_memory()
+    dk = torch.empty_like(hk, device="cuda")
+    dv = torch.empty_like(hv, device="cuda")
+    ws = pdq.workspace_for(n, torch.int32, 4)
+    pdq.pdq_sort_host(hk, dk, ws, h_vals=hv, d_vals=dv)
+    ko, vo = hk.numpy(), hv.numpy().astype(np.int64)
+    assert np.array_equal(ko, np.sort(k))
+    assert np.array_equal(k[vo], ko)
+
+
+@pytest.mark.parametrize("elem", [np.int8, np.int16, np.int32, np.int64])
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 1000, 100_003])
+def test_reverse(elem, n):
+    a = (np.arange(n) * 7 + 3).astype(elem)
+    t = torch.from_numpy(a.copy()).cuda()
+    pdq.pdq_reverse(t)
+    assert np.array_equal(t.cpu().numpy(), a[::-1])
+
+
+def test_sort_on_a_caller_stream():
+    n = 1 << 20
+    a = workloads.uniform_bits(n, np.int32, workloads.config_seed(92))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        d = torch.from_numpy(a.copy()).cuda(non_blocking=False)
+        ws = pdq.workspace_for(n, torch.int32)
+        pdq.pdq_sort_keys(d, ws, stream=s)
+    s.synchronize()
+    assert np.array_equal(d.cpu().numpy(), np.sort(a))
+
+
+def test_workspace_too_small_is_an_error():
+    n = 1 << 20
+    d = to_device(workloads.uniform_bits(n, np.int32, workloads.config_seed(93)))
+    small = torch.empty(1 << 16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(pdq.PdqError) as ei:
+        pdq.pdq_sort_keys(d, small)
+    assert ei.value.status == -3
+
+
+def test_launch_count_and_kernel_profile():
+    n = 1 << 22
+    a = workloads.uniform_bits(n, np.int32, workloads.config_seed(94))
+    d = to_device(a)
+    ws = pdq.workspace_for(n, torch.int32)
+    l0 = pdq.launch_count()
+    pdq.profile_reset()
+    pdq.profile_enable(True)
+    st = pdq.pdq_sort_keys(d, ws)
+    torch.cuda.synchronize()
+    prof = pdq.profile_read()
+    pdq.profile_enable(False)
+    assert pdq.launch_count() - l0 == st["kernel_launches"] > 0
+    for k in ("count", "scatter", "base_sort"):
+        assert k in prof and prof[k][0] > 0 and prof[k][1] >= 1
+    # algorithmic bytes of the base pass: every key outside the equality buckets (a few splitter
+    # values) read and written once
+    assert prof["base_sort"][2] == pytest.approx(2 * 4 * n, rel=1e-2)
+    assert np.array_equal(to_host(d, np.int32), np.sort(a))
