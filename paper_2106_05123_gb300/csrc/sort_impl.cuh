@@ -692,10 +692,13 @@ class PlainSorter {
     if (h.overflow) return set_error(PDQ_ERR_INTERNAL, "bookkeeping list capacity exceeded");
     stats_.equal_buckets += (int64_t)h.equal_buckets;
     stats_.bad_splits += (int64_t)h.bad_splits;
+    // the level's base elements are counted once, on the first class launched
+    int64_t base_elems = (int64_t)h.base_elems;
     for (int cls = 0; cls < kBaseClasses; ++cls) {
       if (!h.n_base[cls]) continue;
-      int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, cls == 0 ? (int64_t)h.base_elems : 0);
+      int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, base_elems);
       if (rc) return rc;
+      base_elems = 0;
     }
     if (h.n_copy) {
       LaunchScope ls("copy", st_, 2.0 * (double)h.copy_elems * (KS + VB));
