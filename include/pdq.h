@@ -87,8 +87,9 @@ typedef struct {
   int32_t inject_wait;      /* test hook, segmented path: one CTA first waits on a flag nothing
                                sets; with a short wait_limit_us the call returns PDQ_ERR_TIMEOUT */
   int32_t seg_block;        /* segmented path: persistent kernel block size, 256 or 512 (default) */
-  int32_t fixup;            /* 1: try the nearly-sorted fix-up when the probe finds few descents
-                               (peel the keys of every descent, sort them, merge; default 0: off) */
+  int32_t fixup;            /* nearly-sorted fix-up when the probe finds few scattered descents
+                               (mark the keys of every descent, repair, sort them apart, merge):
+                               0 default (on), -1 off, 1 on */
 } pdq_tuning;
 
 /* Bytes of workspace the sort of n keys (and a payload of value_bytes, 0 for keys only) needs.

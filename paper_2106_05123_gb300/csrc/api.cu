@@ -118,7 +118,7 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
   d.wait_us = 0;
   d.inject_wait = 0;
   d.seg_block = 512;
-  d.fixup = false;
+  d.fixup = true;
   if (t) {
     if (t->log2_buckets) {
       if (t->log2_buckets < 1 || t->log2_buckets > kLogBMax)
@@ -144,7 +144,7 @@ static int make_tuning(const pdq_tuning* t, Tuning* out) {
     if (t->seg_block && t->seg_block != 256 && t->seg_block != 512)
       return set_error(PDQ_ERR_ARG, "tuning.seg_block must be 256 or 512");
     if (t->seg_block) d.seg_block = t->seg_block;
-    d.fixup = t->fixup > 0;
+    if (t->fixup) d.fixup = t->fixup > 0;
   }
   *out = d;
   return PDQ_OK;

@@ -115,14 +115,26 @@ __global__ void probe_kernel(const typename Key<KT>::U* __restrict__ a, int64_t 
   U mn = ~U(0), mx = U(0);
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gs = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = gt; j < m; j += gs) {
-    const U x = Key<KT>::enc(__ldg(a + j * stride));
-    mn = x < mn ? x : mn;
-    mx = x > mx ? x : mx;
-    if (j + 1 < m) {
-      const U y = Key<KT>::enc(__ldg(a + (j + 1) * stride));
-      desc += x > y;
-      asc += x < y;
+  // eight consecutive sample points per thread and step: nine independent loads in flight
+  constexpr int G = 8;
+  for (int64_t j0 = gt * G; j0 < m; j0 += gs * G) {
+    U v[G + 1];
+#pragma unroll
+    for (int e = 0; e <= G; ++e) {
+      const int64_t j = j0 + e;
+      v[e] = j < m ? Key<KT>::enc(__ldg(a + j * stride)) : U(0);
+    }
+#pragma unroll
+    for (int e = 0; e < G; ++e) {
+      const int64_t j = j0 + e;
+      if (j < m) {
+        mn = v[e] < mn ? v[e] : mn;
+        mx = v[e] > mx ? v[e] : mx;
+        if (j + 1 < m) {
+          desc += v[e] > v[e + 1];
+          asc += v[e] < v[e + 1];
+        }
+      }
     }
   }
   (void)n;
@@ -1204,16 +1216,107 @@ __device__ __forceinline__ bool fix_peeled(const typename Key<KT>::U* __restrict
   return left || right;
 }
 
-// Peeled elements per tile of TILE elements.
-template <int KT, int THREADS, int TILE>
+// Marks both elements of every descent of src[0..len) in the bit mask (bit i of word i / 32):
+// each warp takes four consecutive 32-element words per step, one load per element (the
+// neighbours come by shuffle, the two across the ends by extra loads); *marked receives the
+// number of marked elements.
+template <int KT>
+__global__ void fix_mark_kernel(const typename Key<KT>::U* __restrict__ src, int64_t len, uint32_t* __restrict__ mask,
+                                unsigned long long* __restrict__ marked) {
+  using U = typename Key<KT>::U;
+  constexpr int WPS = 4;  // words per warp step
+  const int lane = threadIdx.x & 31;
+  const int64_t nwords = (len + 31) / 32;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  unsigned long long cnt = 0;
+  for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * WPS; w0 < nwords;
+       w0 += warps * WPS) {
+    U x[WPS];
+#pragma unroll
+    for (int k = 0; k < WPS; ++k) {
+      const int64_t i = (w0 + k) * 32 + lane;
+      x[k] = i < len ? Key<KT>::enc(__ldg(src + i)) : U(0);
+    }
+    const int64_t e0 = w0 * 32 - 1, e1 = (w0 + WPS) * 32;  // neighbours across the step's ends
+    const U before = (e0 >= 0 && e0 < len) ? Key<KT>::enc(__ldg(src + e0)) : U(0);
+    const U after = e1 < len ? Key<KT>::enc(__ldg(src + e1)) : U(0);
+#pragma unroll
+    for (int k = 0; k < WPS; ++k) {
+      const int64_t i = (w0 + k) * 32 + lane;
+      U prev = __shfl_up_sync(0xffffffffu, x[k], 1);
+      U next = __shfl_down_sync(0xffffffffu, x[k], 1);
+      const U last_prev = __shfl_sync(0xffffffffu, k > 0 ? x[k > 0 ? k - 1 : 0] : before, 31);
+      const U first_next = __shfl_sync(0xffffffffu, k + 1 < WPS ? x[k + 1 < WPS ? k + 1 : k] : after, 0);
+      if (lane == 0) prev = k > 0 ? last_prev : before;
+      if (lane == 31) next = k + 1 < WPS ? first_next : after;
+      const bool left = i > 0 && i < len && prev > x[k];
+      const bool right = i + 1 < len && x[k] > next;
+      const uint32_t bits = __ballot_sync(0xffffffffu, left || right);
+      if (w0 + k < nwords && lane == 0) {
+        mask[w0 + k] = bits;
+        cnt += (unsigned long long)__popc(bits);
+      }
+    }
+  }
+  if (lane == 0 && cnt) atomicAdd(marked, cnt);
+}
+
+__device__ __forceinline__ uint32_t fix_word(const uint32_t* mask, int64_t w) { return __ldcg(mask + w); }
+
+// One repair round: for every run of marked elements, its kept neighbours p (before) and q
+// (after) become adjacent once the run is removed; if src[p] > src[q] both are marked.  p is
+// found a word at a time; a run whose kept predecessor lies more than 64 words back marks the
+// round as given up.  Sets *changed when it marked anything; *added counts the marks.
+template <int KT>
+__global__ void fix_repair_kernel(const typename Key<KT>::U* __restrict__ src, int64_t len, uint32_t* __restrict__ mask,
+                                  unsigned int* __restrict__ changed, unsigned int* __restrict__ added) {
+  const int64_t nwords = (len + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = fix_word(mask, w);
+    if (!m) continue;
+    // run ends in this word: marked bits whose successor is unmarked
+    const uint32_t nxt = w + 1 < nwords ? fix_word(mask, w + 1) : ~0u;
+    uint32_t ends = m & ~((m >> 1) | (nxt << 31));
+    while (ends) {
+      const int b = __ffs(ends) - 1;
+      ends &= ends - 1;
+      const int64_t q = w * 32 + b + 1;
+      if (q >= len) continue;
+      // kept predecessor: the highest unmarked bit below the run
+      int64_t pw = w;
+      uint32_t below = ~m & ((1u << b) - 1u);  // unmarked bits below position b
+      int hops = 0;
+      while (!below && pw > 0 && hops < 64) {
+        --pw;
+        ++hops;
+        below = ~fix_word(mask, pw);
+      }
+      if (!below) {
+        if (hops >= 64) atomicOr(changed, 2u);
+        continue;  // no kept predecessor (the run starts the array), or too far
+      }
+      const int64_t p = pw * 32 + (31 - __clz(below));
+      if (Key<KT>::enc(src[p]) > Key<KT>::enc(src[q])) {
+        atomicOr(&mask[p >> 5], 1u << (p & 31));
+        atomicOr(&mask[q >> 5], 1u << (q & 31));
+        atomicOr(changed, 1u);
+        atomicAdd(added, 2u);
+      }
+    }
+  }
+}
+
+// Marked elements per tile of TILE elements (TILE a multiple of 32).
+template <int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS)
-fix_count_kernel(const typename Key<KT>::U* __restrict__ src, int64_t len, uint32_t* __restrict__ tile_cnt) {
+fix_tile_count_kernel(const uint32_t* __restrict__ mask, int64_t len, uint32_t* __restrict__ tile_cnt) {
   __shared__ uint32_t wsum[THREADS / 32];
-  const int64_t t0 = (int64_t)blockIdx.x * TILE;
+  const int64_t w0 = (int64_t)blockIdx.x * (TILE / 32);
+  const int64_t nwords = (len + 31) / 32;
   uint32_t c = 0;
-  for (int j = threadIdx.x; j < TILE; j += THREADS) {
-    const int64_t i = t0 + j;
-    if (i < len) c += fix_peeled<KT>(src, len, i) ? 1u : 0u;
+  for (int j = threadIdx.x; j < TILE / 32; j += THREADS) {
+    const int64_t w = w0 + j;
+    if (w < nwords) c += (uint32_t)__popc(mask[w]);
   }
   c = warp_sum(c);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
@@ -1265,15 +1368,15 @@ fix_scan_kernel(uint32_t* __restrict__ tile_cnt, int ntiles, unsigned long long*
   if (threadIdx.x == 0) *total = carry;
 }
 
-// Kept elements go to dst (in order), peeled ones to pe[e_off + ...] (in order).  Warp w of a
-// tile owns the 32 * PER consecutive elements from t0 + w * 32 * PER; row e of the warp is the
-// 32 consecutive elements base + 32 e + lane (coalesced), ranked by ballots.
+// Elements whose mask bit is clear go to dst (in order), marked ones to pe[e_off + ...] (in
+// order).  Warp w of a tile owns the 32 * PER consecutive elements from t0 + w * 32 * PER; row e
+// of the warp is the 32 consecutive elements base + 32 e + lane (coalesced) and one mask word.
 template <int KT, int VB, int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS)
 fix_compact_kernel(const typename Key<KT>::U* __restrict__ src, const typename Val<VB>::T* __restrict__ srcv,
-                   int64_t len, typename Key<KT>::U* __restrict__ dst, typename Val<VB>::T* __restrict__ dstv,
-                   typename Key<KT>::U* __restrict__ pe, typename Val<VB>::T* __restrict__ pev, int64_t e_off,
-                   const uint32_t* __restrict__ tile_pre) {
+                   int64_t len, const uint32_t* __restrict__ bits, typename Key<KT>::U* __restrict__ dst,
+                   typename Val<VB>::T* __restrict__ dstv, typename Key<KT>::U* __restrict__ pe,
+                   typename Val<VB>::T* __restrict__ pev, int64_t e_off, const uint32_t* __restrict__ tile_pre) {
   constexpr int NW = THREADS / 32;
   constexpr int PER = TILE / THREADS;  // rows per warp
   static_assert(TILE % THREADS == 0 && PER <= 32, "tile shape");
@@ -1285,7 +1388,9 @@ fix_compact_kernel(const typename Key<KT>::U* __restrict__ src, const typename V
 #pragma unroll
   for (int e = 0; e < PER; ++e) {
     const int64_t i = base + 32 * e + lane;
-    mask[e] = __ballot_sync(0xffffffffu, i < len && fix_peeled<KT>(src, len, i));
+    const int64_t r0 = base + 32 * e;  // rows are 32-aligned: one mask word each (warp-uniform)
+    mask[e] = r0 < len ? bits[r0 >> 5] : 0u;
+    (void)i;
     peeled += (uint32_t)__popc(mask[e]);
   }
   if (lane == 0) wcnt[warp] = peeled;
@@ -1293,69 +1398,190 @@ fix_compact_kernel(const typename Key<KT>::U* __restrict__ src, const typename V
   uint32_t before = tile_pre[blockIdx.x];  // peeled elements before this warp's range
   for (int w = 0; w < warp; ++w) before += wcnt[w];
   const uint32_t lt = (1u << lane) - 1u;
+  constexpr int G = 8;  // rows loaded ahead: G independent loads in flight per thread
 #pragma unroll
-  for (int e = 0; e < PER; ++e) {
-    const int64_t i = base + 32 * e + lane;
-    const uint32_t p = before + (uint32_t)__popc(mask[e] & lt);  // peeled before element i
-    if (i < len) {
-      if ((mask[e] >> lane) & 1u) {
-        pe[e_off + p] = src[i];
-        if (VB) pev[e_off + p] = srcv[i];
-      } else {
-        dst[i - p] = src[i];
-        if (VB) dstv[i - p] = srcv[i];
+  for (int e0 = 0; e0 < PER; e0 += G) {
+    typename Key<KT>::U kx[G];
+    typename Val<VB>::T vx[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t i = base + 32 * (e0 + g) + lane;
+      if (e0 + g < PER && i < len) {
+        kx[g] = src[i];
+        if (VB) vx[g] = srcv[i];
       }
     }
-    before += (uint32_t)__popc(mask[e]);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int e = e0 + g;
+      if (e < PER) {
+        const int64_t i = base + 32 * e + lane;
+        const uint32_t p = before + (uint32_t)__popc(mask[e] & lt);  // marked before element i
+        if (i < len) {
+          if ((mask[e] >> lane) & 1u) {
+            pe[e_off + p] = kx[g];
+            if (VB) pev[e_off + p] = vx[g];
+          } else {
+            dst[i - p] = kx[g];
+            if (VB) dstv[i - p] = vx[g];
+          }
+        }
+        before += (uint32_t)__popc(mask[e]);
+      }
+    }
   }
 }
 
-// Merge of two ascending arrays (raw keys, compared by their codes) into out[0..la+lb): each
-// thread finds its merge-path split for ITEMS outputs by binary search, merges them into shared
-// memory, and the block writes its THREADS * ITEMS outputs with coalesced stores.  Ties take A.
+// ================================================================== tiled merge
+// Merges ascending runs by tiles of TILE = THREADS * ITEMS outputs per CTA (merge path, Odeh et
+// al. 2012): the CTA finds where its tile starts and ends on the merge path of its pair by two
+// binary searches in global memory, loads both input ranges into shared memory with coalesced
+// reads, every thread merges ITEMS outputs from shared memory, and the tile is stored coalesced.
+// Pairs: with w > 0 the runs of width w of one array a[0..n) are merged pairwise (2w a multiple
+// of TILE); with w == 0 the single pair is a[0..la) and b[0..lb).  raw: inputs are keys (compared
+// by their codes, and written back as keys); otherwise they are codes, written decoded when
+// `decode` is set.  Ties take A.
+template <int KT, int VB>
+struct MergeArgs {
+  const typename Key<KT>::U* a;
+  const typename Val<VB>::T* av;
+  int64_t la;
+  const typename Key<KT>::U* b;
+  const typename Val<VB>::T* bv;
+  int64_t lb;
+  typename Key<KT>::U* out;
+  typename Val<VB>::T* outv;
+  int64_t w;  // 0: one pair (a, b); > 0: pairwise runs of a[0..n)
+  int64_t n;
+  int raw;
+  int decode;
+};
+
+template <int KS, int VB, int THREADS, int ITEMS>
+constexpr size_t merge_tile_smem() {
+  return (size_t)2 * THREADS * ITEMS * (KS + VB);
+}
+
+// The pair a tile of the merge belongs to: its runs A, B and its first output p0.
+template <int KT, int VB>
+struct MergePair {
+  const typename Key<KT>::U* A;
+  const typename Val<VB>::T* Av;
+  const typename Key<KT>::U* B;
+  const typename Val<VB>::T* Bv;
+  int64_t la, lb, p0;
+};
+template <int KT, int VB>
+__device__ __forceinline__ MergePair<KT, VB> merge_pair_of(const MergeArgs<KT, VB>& m, int64_t t0) {
+  MergePair<KT, VB> q;
+  if (m.w > 0) {
+    q.p0 = t0 / (2 * m.w) * (2 * m.w);
+    q.la = m.n - q.p0 < m.w ? m.n - q.p0 : m.w;
+    q.lb = m.n - q.p0 - q.la < m.w ? m.n - q.p0 - q.la : m.w;
+    if (q.lb < 0) q.lb = 0;
+    q.A = m.a + q.p0;
+    q.Av = VB ? m.av + q.p0 : nullptr;
+    q.B = q.A + q.la;
+    q.Bv = VB ? q.Av + q.la : nullptr;
+  } else {
+    q.p0 = 0;
+    q.la = m.la;
+    q.lb = m.lb;
+    q.A = m.a;
+    q.Av = m.av;
+    q.B = m.b;
+    q.Bv = m.bv;
+  }
+  return q;
+}
+
+// Merge-path split (A elements among the first d outputs of the tile's pair) at the start of
+// every tile, one thread per tile, all searches in parallel.
+template <int KT, int VB, int TILE>
+__global__ void merge_split_kernel(MergeArgs<KT, VB> m, int64_t ntiles, int64_t* __restrict__ splits) {
+  using U = typename Key<KT>::U;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const MergePair<KT, VB> q = merge_pair_of(m, t * TILE);
+  auto code = [&](U x) { return m.raw ? Key<KT>::enc(x) : x; };
+  const int64_t d = t * TILE - q.p0;
+  int64_t lo = d > q.lb ? d - q.lb : 0, hi = d < q.la ? d : q.la;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (!(code(q.B[d - 1 - mid]) < code(q.A[mid]))) lo = mid + 1;
+    else hi = mid;
+  }
+  splits[t] = lo;
+}
+
 template <int KT, int VB, int THREADS, int ITEMS>
 __global__ void __launch_bounds__(THREADS)
-fix_merge_kernel(const typename Key<KT>::U* __restrict__ A, const typename Val<VB>::T* __restrict__ Av, int64_t la,
-                 const typename Key<KT>::U* __restrict__ B, const typename Val<VB>::T* __restrict__ Bv, int64_t lb,
-                 typename Key<KT>::U* __restrict__ out, typename Val<VB>::T* __restrict__ outv) {
+merge_tile_kernel(MergeArgs<KT, VB> m, const int64_t* __restrict__ splits) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
-  constexpr int BLK = THREADS * ITEMS;
-  __shared__ U sk[BLK];
-  __shared__ V sv[VB ? BLK : 1];
-  const int64_t total = la + lb;
-  const int64_t b0 = (int64_t)blockIdx.x * BLK;
-  const int64_t d = b0 + (int64_t)threadIdx.x * ITEMS;
+  constexpr int TILE = THREADS * ITEMS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  U* sin = reinterpret_cast<U*>(smem);          // A range then B range (codes)
+  U* sout = sin + TILE;                         // merged tile (codes)
+  V* sinv = reinterpret_cast<V*>(sout + TILE);
+  V* soutv = sinv + TILE;
+
+  const int64_t t0 = (int64_t)blockIdx.x * TILE;
+  const MergePair<KT, VB> q = merge_pair_of(m, t0);
+  const U* A = q.A;
+  const V* Av = q.Av;
+  const U* B = q.B;
+  const V* Bv = q.Bv;
+  const int64_t la = q.la, lb = q.lb, p0 = q.p0;
+  auto code = [&](U x) { return m.raw ? Key<KT>::enc(x) : x; };
+  const int64_t d0 = t0 - p0;
+  const int64_t d1 = d0 + TILE < la + lb ? d0 + TILE : la + lb;
+  // the tile ends where the next one starts, or at the end of its pair (all of A consumed)
+  const int64_t a_lo = splits[blockIdx.x], a_hi = d1 == la + lb ? la : splits[blockIdx.x + 1];
+  const int na = (int)(a_hi - a_lo), nb = (int)((d1 - a_hi) - (d0 - a_lo));
+  const int64_t b_lo = d0 - a_lo;
+  for (int j = threadIdx.x; j < na; j += THREADS) {
+    sin[j] = code(A[a_lo + j]);
+    if (VB) sinv[j] = Av[a_lo + j];
+  }
+  for (int j = threadIdx.x; j < nb; j += THREADS) {
+    sin[na + j] = code(B[b_lo + j]);
+    if (VB) sinv[na + j] = Bv[b_lo + j];
+  }
+  __syncthreads();
+  const int total = na + nb;
+  const int d = threadIdx.x * ITEMS;
   if (d < total) {
-    int64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    const U* sa = sin;
+    const U* sb = sin + na;
+    int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
     while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (!(Key<KT>::enc(B[d - 1 - mid]) < Key<KT>::enc(A[mid]))) lo = mid + 1;
+      const int mid = (lo + hi) >> 1;
+      if (!(sb[d - 1 - mid] < sa[mid])) lo = mid + 1;
       else hi = mid;
     }
-    int64_t ia = lo, ib = d - lo;
-    const int cnt = (int)(total - d < ITEMS ? total - d : ITEMS);
-    for (int e = 0; e < cnt; ++e) {
-      const bool take_a = ia < la && (ib >= lb || !(Key<KT>::enc(B[ib]) < Key<KT>::enc(A[ia])));
-      const int s = threadIdx.x * ITEMS + e;
-      if (take_a) {
-        sk[s] = A[ia];
-        if (VB) sv[s] = Av[ia];
-        ++ia;
-      } else {
-        sk[s] = B[ib];
-        if (VB) sv[s] = Bv[ib];
-        ++ib;
+    int ia = lo, ib = d - lo;
+    const int cnt = total - d < ITEMS ? total - d : ITEMS;
+#pragma unroll
+    for (int e = 0; e < ITEMS; ++e) {
+      if (e < cnt) {
+        const bool take_a = ia < na && (ib >= nb || !(sb[ib] < sa[ia]));
+        const int src = take_a ? ia : na + ib;
+        sout[d + e] = sin[src];
+        if (VB) soutv[d + e] = sinv[src];
+        ia += take_a ? 1 : 0;
+        ib += take_a ? 0 : 1;
       }
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < BLK; j += THREADS) {
-    const int64_t o = b0 + j;
-    if (o < total) {
-      out[o] = sk[j];
-      if (VB) outv[o] = sv[j];
-    }
+  U* out = m.out + p0 + d0;
+  V* outv = VB ? m.outv + p0 + d0 : nullptr;
+  const bool dec = m.raw || m.decode;
+  for (int j = threadIdx.x; j < total; j += THREADS) {
+    const U c = sout[j];
+    out[j] = dec ? Key<KT>::dec(c) : c;
+    if (VB) outv[j] = soutv[j];
   }
 }
 

@@ -36,7 +36,7 @@ struct SortArgs {
 // Byte offsets of the workspace regions.
 struct Layout {
   size_t tmpk, tmpv, ctr, tasks_cur, tasks_next, task_meta, chunks, counts, tree, spl, children,
-      pref, tab, base_items, copy_items, fb_items, total;
+      pref, tab, base_items, copy_items, fb_items, msplit, total;
   int64_t task_cap, round_cap, chunk_cap, item_cap, fb_cap;
   int64_t base_off[5];  // first entry of each base-sort size class's list (in items)
   int64_t base_cap[5];  // capacity of each class's list
@@ -44,7 +44,7 @@ struct Layout {
   int64_t learned_m;
   // nearly-sorted fix-up (absent in nested sorts and below kFixMin elements): peeled keys and
   // values (up to fix_m), per-tile counts, and the workspace of the peeled keys' own sort
-  size_t fix_e, fix_ev, fix_cnt, fix_ws, fix_ws_bytes;
+  size_t fix_e, fix_ev, fix_cnt, fix_mask, fix_ws, fix_ws_bytes;
   int64_t fix_m;
 };
 

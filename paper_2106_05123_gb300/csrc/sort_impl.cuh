@@ -67,6 +67,7 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
   L.base_items = take((size_t)base_total * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
+  L.msplit = take((size_t)(n / 2048 + 2) * sizeof(int64_t));  // merge-path splits, one per 2048-output tile
   if (learned) {  // 1% training sample and the trained model (learned path, float32 keys)
     L.learned_m = std::min<int64_t>(n, std::max<int64_t>(4096, n / 100));
     L.learned_xs = take((size_t)L.learned_m * sizeof(float));
@@ -78,6 +79,7 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
     L.fix_e = take((size_t)(L.fix_m + 16) * ks);
     L.fix_ev = take((size_t)(L.fix_m + 16) * vb);
     L.fix_cnt = take((size_t)(n / kFixTile + 2) * sizeof(uint32_t));
+    L.fix_mask = take((size_t)(n / 32 + 2) * sizeof(uint32_t));
     L.fix_ws_bytes = make_layout(L.fix_m, ks, vb, false, false).total;
     L.fix_ws = take(L.fix_ws_bytes);
   }
@@ -398,6 +400,9 @@ class PlainSorter {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kScatterSmem));
     PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kCountSmem));
+    PDQ_CUDA(cudaFuncSetAttribute(merge_tile_kernel<KT, VB, kMergeThreads, kMergeItems>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)merge_tile_smem<KS, VB, kMergeThreads, kMergeItems>()));
     int rc = configure_base<0>();
     if (!rc) rc = configure_base<1>();
     if (!rc) rc = configure_base<2>();
@@ -436,8 +441,12 @@ class PlainSorter {
     int rc = run_probe(stride);
     if (rc) return rc;
     const int64_t m_sample = (n - 1) / stride + 1;
-    // the sample is neither monotone: unless its descents are few (nearly ascending), sort
-    if (stride > 1 && h[0] != 0 && h[1] != 0 && !(can_fix && (int64_t)h[0] * 16 <= m_sample)) return PDQ_OK;
+    // The sample is neither monotone: sort, unless its descents are few (at most 1/16 of its
+    // pairs) yet scattered (at least 1/256: not a handful of long ascending runs, whose
+    // boundaries the fix-up cannot repair) -- then probe the whole array for the fix-up.
+    if (stride > 1 && h[0] != 0 && h[1] != 0 &&
+        !(can_fix && (int64_t)h[0] * 16 <= m_sample && (int64_t)h[0] * 256 >= m_sample))
+      return PDQ_OK;
     if (stride > 1) {
       rc = run_probe(1);
       if (rc) return rc;
@@ -461,14 +470,18 @@ class PlainSorter {
       PDQ_LAUNCHED("reverse");
       return PDQ_OK;
     }
-    if (can_fix && (int64_t)h[0] <= n / 32) *nearly = true;  // few descents: the fix-up
+    // Few descents, but not so few that the input is a handful of long ascending runs (whose
+    // boundaries peeling cannot repair): the fix-up.
+    if (can_fix && (int64_t)h[0] <= n / 32 && (int64_t)h[0] >= n / 4096) *nearly = true;
     return PDQ_OK;
   }
 
-  // Nearly-sorted fix-up: peel both elements of every descent into E (at most fix_m, at most
-  // six rounds, each at most half the previous) until the remainder R has no descent, sort E on its own, merge R and E into the
-  // key buffer.  *fixed is false when the bounds are hit: the arrays then hold R followed by E
-  // (a permutation of the input) and the caller sorts them the ordinary way.
+  // Nearly-sorted fix-up: mark both elements of every descent; then, in repair rounds that
+  // only look at the kept neighbours of each marked run, mark them too while they are out of
+  // order, until the unmarked elements are ascending (at most 16 rounds, at most fix_m marked).
+  // Only then is anything moved: one compaction splits the array into the ascending remainder R
+  // and the marked elements E, E is sorted on its own, and R and E are merged into the key
+  // buffer.  *fixed is false when a bound is hit: nothing has moved, the caller sorts as usual.
   int fixup(bool* fixed) {
     *fixed = false;
     const int64_t n = a_.n;
@@ -476,61 +489,73 @@ class PlainSorter {
     U* E = reinterpret_cast<U*>(ws + L_.fix_e);
     V* Ev = reinterpret_cast<V*>(ws + L_.fix_ev);
     uint32_t* tc = reinterpret_cast<uint32_t*>(ws + L_.fix_cnt);
-    U* cur = keys_ + off_;
-    V* curv = VB ? vals_ + off_ : nullptr;
-    U* oth = tmpk_ + off_;
-    V* othv = VB ? tmpv_ + off_ : nullptr;
-    int64_t len = n, e_len = 0;
-    bool clean = false, over = false;
-    unsigned long long r_prev = 0;
-    for (int round = 0; round < 6; ++round) {
-      const int ntiles = (int)((len + kFixTile - 1) / kFixTile);
+    uint32_t* mask = reinterpret_cast<uint32_t*>(ws + L_.fix_mask);
+    U* src = keys_ + off_;
+    V* srcv = VB ? vals_ + off_ : nullptr;
+    unsigned long long* marked = &ctr_->probe[4];
+    unsigned int* changed = reinterpret_cast<unsigned int*>(&ctr_->probe[5]);
+    PDQ_CUDA(cudaMemsetAsync(marked, 0, sizeof(unsigned long long), st_));
+    {
+      LaunchScope ls("fixup_mark", st_, (double)n * KS);
+      const int64_t words = (n + 31) / 32;
+      const unsigned blocks = (unsigned)std::min<int64_t>((words + 7) / 8, (int64_t)a_.num_sms * 16);
+      fix_mark_kernel<KT><<<blocks, 256, 0, st_>>>(src, n, mask, marked);
+    }
+    PDQ_LAUNCHED("fixup_mark");
+    unsigned long long h[2] = {0, 0};
+    PDQ_CUDA(cudaMemcpyAsync(h, marked, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st_));
+    PDQ_CUDA(cudaStreamSynchronize(st_));
+    if ((int64_t)h[0] > L_.fix_m) return PDQ_OK;
+    bool clean = false;
+    unsigned int* added = changed + 1;
+    unsigned int prev_added = 0;
+    for (int round = 0; round < 16; ++round) {
+      PDQ_CUDA(cudaMemsetAsync(changed, 0, 2 * sizeof(unsigned int), st_));
       {
-        LaunchScope ls("fixup_peel", st_, (double)len * KS);
-        fix_count_kernel<KT, 256, kFixTile><<<ntiles, 256, 0, st_>>>(cur, len, tc);
-        fix_scan_kernel<1024><<<1, 1024, 0, st_>>>(tc, ntiles, &ctr_->probe[4]);
-        note_launch_count(1);
+        LaunchScope ls("fixup_repair", st_, 0.0);
+        const int64_t words = (n + 31) / 32;
+        const unsigned blocks = (unsigned)std::min<int64_t>((words + 255) / 256, (int64_t)a_.num_sms * 8);
+        fix_repair_kernel<KT><<<blocks, 256, 0, st_>>>(src, n, mask, changed, added);
       }
-      PDQ_LAUNCHED("fixup_peel");
-      unsigned long long r = 0;
-      PDQ_CUDA(cudaMemcpyAsync(&r, &ctr_->probe[4], sizeof(r), cudaMemcpyDeviceToHost, st_));
+      PDQ_LAUNCHED("fixup_repair");
+      unsigned int c[2] = {0, 0};
+      PDQ_CUDA(cudaMemcpyAsync(c, changed, sizeof(c), cudaMemcpyDeviceToHost, st_));
       PDQ_CUDA(cudaStreamSynchronize(st_));
-      if (r == 0) {
+      if (c[0] & 2u) break;  // a marked run too long to repair locally
+      if (c[0] == 0) {
         clean = true;
         break;
       }
-      // give up past the side array's capacity, or when a round does not at least halve the
-      // previous one (long ascending runs: peeling only moves their boundaries)
-      if (e_len + (int64_t)r > L_.fix_m || (round > 0 && 2 * r > r_prev)) {
-        over = true;
-        break;
-      }
-      r_prev = r;
-      {
-        LaunchScope ls("fixup_compact", st_, 2.0 * (double)len * (KS + VB));
-        fix_compact_kernel<KT, VB, 256, kFixTile><<<ntiles, 256, 0, st_>>>(cur, curv, len, oth, othv, E, Ev, e_len, tc);
-      }
-      PDQ_LAUNCHED("fixup_compact");
-      e_len += (int64_t)r;
-      len -= (int64_t)r;
-      std::swap(cur, oth);
-      std::swap(curv, othv);
+      // a first repair that marks more than an eighth again (a shuffled stretch), or rounds
+      // that stop shrinking (long ascending runs grow their junctions steadily): give up
+      if (round == 0 && (uint64_t)c[1] * 8 > (uint64_t)h[0]) break;
+      if (round >= 1 && (uint64_t)c[1] * 10 >= (uint64_t)prev_added * 9) break;
+      prev_added = c[1];
     }
-    const bool in_keys = cur == keys_ + off_;
-    if (!clean || over) {
-      // give up: the key buffer gets R then E, a permutation of the input
-      if (!in_keys) {
-        PDQ_CUDA(cudaMemcpyAsync(keys_ + off_, cur, (size_t)len * KS, cudaMemcpyDeviceToDevice, st_));
-        if (VB) PDQ_CUDA(cudaMemcpyAsync(vals_ + off_, curv, (size_t)len * VB, cudaMemcpyDeviceToDevice, st_));
-      }
-      if (e_len) {
-        PDQ_CUDA(cudaMemcpyAsync(keys_ + off_ + len, E, (size_t)e_len * KS, cudaMemcpyDeviceToDevice, st_));
-        if (VB) PDQ_CUDA(cudaMemcpyAsync(vals_ + off_ + len, Ev, (size_t)e_len * VB, cudaMemcpyDeviceToDevice, st_));
-      }
-      return PDQ_OK;
+    if (!clean) return PDQ_OK;
+    // marked elements per tile, their exclusive prefix (total = |E|), then the split
+    const int ntiles = (int)((n + kFixTile - 1) / kFixTile);
+    {
+      LaunchScope ls("fixup_split", st_, 2.0 * (double)n * (KS + VB));
+      fix_tile_count_kernel<256, kFixTile><<<ntiles, 256, 0, st_>>>(mask, n, tc);
+      fix_scan_kernel<1024><<<1, 1024, 0, st_>>>(tc, ntiles, marked);
+      note_launch_count(1);
     }
+    PDQ_LAUNCHED("fixup_split");
+    PDQ_CUDA(cudaMemcpyAsync(h, marked, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st_));
+    PDQ_CUDA(cudaStreamSynchronize(st_));
+    const int64_t e_len = (int64_t)h[0];
+    if (e_len > L_.fix_m) return PDQ_OK;
+    U* R = tmpk_ + off_;
+    V* Rv = VB ? tmpv_ + off_ : nullptr;
+    const int64_t len = n - e_len;
+    {
+      LaunchScope ls("fixup_compact", st_, 2.0 * (double)n * (KS + VB));
+      fix_compact_kernel<KT, VB, 256, kFixTile><<<ntiles, 256, 0, st_>>>(src, srcv, n, mask, R, Rv, E, Ev, 0, tc);
+    }
+    PDQ_LAUNCHED("fixup_compact");
     stats_.fixup_peeled = e_len;
-    if (e_len > 1) {  // the peeled keys' own sort (no fix-up inside it)
+    if (e_len > 1) {  // the marked keys' own sort (no fix-up inside it)
       SortArgs sa = a_;
       sa.keys = E;
       sa.vals = VB ? static_cast<void*>(Ev) : nullptr;
@@ -545,18 +570,22 @@ class PlainSorter {
       stats_.equal_buckets += sub.stats_.equal_buckets;
       stats_.fallback_buckets += sub.stats_.fallback_buckets;
     }
-    if (in_keys) {  // the merge writes the key buffer, so R moves out of it first
-      PDQ_CUDA(cudaMemcpyAsync(tmpk_ + off_, cur, (size_t)len * KS, cudaMemcpyDeviceToDevice, st_));
-      if (VB) PDQ_CUDA(cudaMemcpyAsync(tmpv_ + off_, curv, (size_t)len * VB, cudaMemcpyDeviceToDevice, st_));
-      cur = tmpk_ + off_;
-      curv = VB ? tmpv_ + off_ : nullptr;
-    }
     {
-      constexpr int kMT = 256, kMI = 8;
-      const int64_t blocks = (n + kMT * kMI - 1) / (kMT * kMI);
+      MergeArgs<KT, VB> ma;
+      ma.a = R;
+      ma.av = Rv;
+      ma.la = len;
+      ma.b = E;
+      ma.bv = Ev;
+      ma.lb = e_len;
+      ma.out = keys_ + off_;
+      ma.outv = VB ? vals_ + off_ : nullptr;
+      ma.w = 0;
+      ma.n = n;
+      ma.raw = 1;
+      ma.decode = 0;
       LaunchScope ls("fixup_merge", st_, 2.0 * (double)n * (KS + VB));
-      fix_merge_kernel<KT, VB, kMT, kMI><<<(unsigned)blocks, kMT, 0, st_>>>(cur, curv, len, E, Ev, e_len,
-                                                                           keys_ + off_, VB ? vals_ + off_ : nullptr);
+      launch_merge_tiles(ma, n);
     }
     PDQ_LAUNCHED("fixup_merge");
     *fixed = true;
@@ -743,6 +772,16 @@ class PlainSorter {
     return PDQ_OK;
   }
 
+  static constexpr int kMergeThreads = 256, kMergeItems = 8, kMergeTile = kMergeThreads * kMergeItems;
+  void launch_merge_tiles(const MergeArgs<KT, VB>& ma, int64_t total) {
+    constexpr size_t smem = merge_tile_smem<KS, VB, kMergeThreads, kMergeItems>();
+    const int64_t blocks = (total + kMergeTile - 1) / kMergeTile;
+    int64_t* splits = reinterpret_cast<int64_t*>(static_cast<char*>(a_.ws) + L_.msplit);
+    merge_split_kernel<KT, VB, kMergeTile><<<(unsigned)((blocks + 255) / 256), 256, 0, st_>>>(ma, blocks, splits);
+    merge_tile_kernel<KT, VB, kMergeThreads, kMergeItems><<<(unsigned)blocks, kMergeThreads, smem, st_>>>(ma, splits);
+    note_launch_count(1);
+  }
+
   int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems) {
     stats_.base_buckets += count;
     switch (cls) {
@@ -790,10 +829,27 @@ class PlainSorter {
       V* sv = VB ? (cur == kBufKeys ? vals_ : tmpv_) + it.begin : nullptr;
       U* dk = (cur == kBufKeys ? tmpk_ : keys_) + it.begin;
       V* dv = VB ? (cur == kBufKeys ? tmpv_ : vals_) + it.begin : nullptr;
-      const unsigned blocks = (unsigned)(((int64_t)it.size + 255) / 256);
       {
         LaunchScope ls("merge_pass", st_, 2.0 * (double)it.size * (KS + VB));
-        merge_pass_kernel<KT, VB><<<blocks, 256, 0, st_>>>(sk, sv, dk, dv, (int64_t)it.size, w, p == passes ? 1 : 0);
+        if (2 * w >= kMergeTile) {  // pairs span whole tiles: the tiled merge
+          MergeArgs<KT, VB> ma;
+          ma.a = sk;
+          ma.av = sv;
+          ma.la = 0;
+          ma.b = nullptr;
+          ma.bv = nullptr;
+          ma.lb = 0;
+          ma.out = dk;
+          ma.outv = dv;
+          ma.w = w;
+          ma.n = (int64_t)it.size;
+          ma.raw = 0;
+          ma.decode = p == passes ? 1 : 0;
+          launch_merge_tiles(ma, (int64_t)it.size);
+        } else {
+          const unsigned blocks = (unsigned)(((int64_t)it.size + 255) / 256);
+          merge_pass_kernel<KT, VB><<<blocks, 256, 0, st_>>>(sk, sv, dk, dv, (int64_t)it.size, w, p == passes ? 1 : 0);
+        }
       }
       PDQ_LAUNCHED("merge_pass");
       cur = 1 - cur;

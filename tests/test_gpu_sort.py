@@ -208,8 +208,10 @@ def test_nearly_sorted_fixup_exact(dtype, n):
     oracle.pdqsort(want)
     assert np.array_equal(bits(got), bits(want))
     assert st["fixup_peeled"] > 0
-    _, _, st_off = gpu_sort(a)  # off by default
-    assert st_off["fixup_peeled"] == 0
+    _, _, st_on = gpu_sort(a)  # on by default
+    assert st_on["fixup_peeled"] > 0
+    got_off, _, st_off = gpu_sort(a, tuning={"fixup": -1})
+    assert st_off["fixup_peeled"] == 0 and np.array_equal(bits(got_off), bits(want))
 
 
 @pytest.mark.parametrize("name", ["sort99", "merge", "sawtooth", "asc_swaps"])
