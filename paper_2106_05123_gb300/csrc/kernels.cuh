@@ -170,12 +170,26 @@ __global__ void probe_kernel(const typename Key<KT>::U* __restrict__ a, int64_t 
 template <class T>
 __global__ void reverse_kernel(T* __restrict__ a, int64_t n) {
   const int64_t half = n / 2;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < half;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = n - 1 - i;
-    const T x = a[i], y = a[j];
-    a[i] = y;
-    a[j] = x;
+  constexpr int G = 4;  // swaps per thread and step, loaded before any is stored
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < half; i0 += G * step) {
+    T x[G], y[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t i = i0 + g * step;
+      if (i < half) {
+        x[g] = a[i];
+        y[g] = a[n - 1 - i];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int64_t i = i0 + g * step;
+      if (i < half) {
+        a[i] = y[g];
+        a[n - 1 - i] = x[g];
+      }
+    }
   }
 }
 
