@@ -18,7 +18,10 @@
 //                       more than 7/8 of its parent is a bad split and decrements the subtree's
 //                       counter; at 0 the bin goes to the fallback (Sec. 4.1)
 //   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1)
-//   merge_pass_kernel - merge-path merge pass of the O(n log n) fallback (Sec. 4.1)
+//   merge_tile_kernel - tiled merge-path merge (the O(n log n) fallback's passes, Sec. 4.1, and
+//                       the nearly-sorted fix-up's final merge); merge_pass_kernel serves
+//                       passes whose run pairs are shorter than a tile
+//   fix_*_kernel      - the nearly-sorted fix-up: mark descents, repair, split (Sec. 5.2's aim)
 #pragma once
 
 #include "common.cuh"
@@ -228,9 +231,6 @@ __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, co
 // When b_hi <= b_lo + 1 the entry's candidate s0 = spl[b_lo] settles both the rank
 // (b_lo + [s0 < code]) and the equality test (code == s0): splitter b_lo + 1, if any, lies above
 // the slice and so cannot equal a code in it.
-constexpr int kPrefBitsMax = 11;
-constexpr int kPrefEntriesMax = 1 << kPrefBitsMax;
-
 // Table size per key width: 2048 entries of 8 bytes (4-byte codes) or 1024 of 16 bytes.
 template <class U>
 __host__ __device__ constexpr int pref_bits() { return sizeof(U) == 4 ? 11 : 10; }
@@ -1216,19 +1216,11 @@ __global__ void copy_kernel(const Item* __restrict__ items, typename Key<KT>::U*
 }
 
 // ================================================================== nearly-sorted fix-up
-// For input with few descents (Sec. 5.2's partial insertion sort has the same aim: finish an
-// almost sorted range in linear time).  Both elements of every descent are peeled off into a
-// side array E until the remainder R has no descent; E is sorted on its own, and R and E are
-// merged.  Element i of src[0..len) is peeled when src[i-1] > src[i] or src[i] > src[i+1]
-// (order of the encoded codes).
-template <int KT>
-__device__ __forceinline__ bool fix_peeled(const typename Key<KT>::U* __restrict__ src, int64_t len, int64_t i) {
-  using U = typename Key<KT>::U;
-  const U x = Key<KT>::enc(src[i]);
-  const bool left = i > 0 && Key<KT>::enc(src[i - 1]) > x;
-  const bool right = i + 1 < len && x > Key<KT>::enc(src[i + 1]);
-  return left || right;
-}
+// For input with few scattered descents (Sec. 5.2's partial insertion sort has the same aim:
+// finish an almost sorted range in linear time).  Both elements of every descent are marked,
+// repair rounds extend the marks until the unmarked elements R are ascending, one split moves R
+// and the marked elements E apart, E is sorted on its own, and R and E are merged.  Comparisons
+// are of the encoded codes.
 
 // Marks both elements of every descent of src[0..len) in the bit mask (bit i of word i / 32):
 // each warp takes four consecutive 32-element words per step, one load per element (the
