@@ -150,12 +150,16 @@ def measured_peak_gbs() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+# Sources that define the plain path's kernels and their launch shapes (device code, tile and
+# chunk sizes, workspace layout); a DRAM-traffic figure is valid only for these exact files.
+KERNEL_SOURCES = ("common.cuh", "tile_pipe.cuh", "kernels.cuh", "sort_impl.cuh", "sort_api.h", "learned.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_05123_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -1,5 +1,6 @@
 // C ABI of the library (see include/pdq.h): argument checks, dtype dispatch, error strings,
 // launch counting and the optional per-kernel event timing used for measurement.
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -43,6 +44,7 @@ static thread_local std::vector<Pending> t_open;
 
 void note_launch(const char* name, cudaStream_t s, double bytes) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  nvtxRangePushA(name);  // a named range per launch for timeline tools (no-op when none attached)
   if (!g_profile.load(std::memory_order_relaxed)) return;
   Pending p;
   p.name = name;
@@ -54,6 +56,7 @@ void note_launch(const char* name, cudaStream_t s, double bytes) {
 }
 
 void note_launch_end(const char* name, cudaStream_t s) {
+  nvtxRangePop();
   if (t_open.empty()) return;
   Pending p = t_open.back();
   t_open.pop_back();
