@@ -378,7 +378,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
   for (int k = 2; k <= ns; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int q = threadIdx.x; q < ns / 2; q += THREADS) {
-        const int i = (q / j) * 2 * j + (q % j);
+        const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));  // j is a power of two
         const int l = i + j;
         const bool up = (i & k) == 0;
         const U a = s[i], b = s[l];

@@ -230,7 +230,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
   for (int k = 2; k <= ns; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int q = tid; q < ns / 2; q += THREADS) {
-        const int i = (q / j) * 2 * j + (q % j);
+        const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));  // j is a power of two
         const int l = i + j;
         const bool up = (i & k) == 0;
         const U a = s[i], b = s[l];

@@ -248,3 +248,43 @@ def test_nearly_sorted_clustered_displacements(kind):
     want = a.copy()
     oracle.pdqsort(want)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.uint64])
+@pytest.mark.parametrize("lo,hi", [(1, 0), (3, -2)])
+def test_nearly_sorted_fixup_on_misaligned_subarrays(dtype, lo, hi):
+    """The fix-up on a slice that starts off a 16-byte boundary, keys and pairs: only the slice
+    changes, bit-exact, values attached."""
+    import torch
+    import paper_2106_05123_gb300 as pdq
+    from gpu_helpers import CODE, to_device, to_host
+    n = 700_001
+    a = workloads.pattern("asc_swaps", n, workloads.config_seed(82), dtype=np.int64).astype(dtype)
+    end = n + hi if hi else n
+    want = a.copy()
+    want[lo:end] = np.sort(a[lo:end])
+    d = to_device(a)
+    st = pdq.pdq_sort_keys(d[lo:end], key_dtype=CODE[np.dtype(dtype)])
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(d, dtype), want)
+    assert st["fixup_peeled"] > 0
+    v = np.arange(n, dtype=np.uint32 if np.dtype(dtype).itemsize == 4 else np.uint64)
+    dk, dv = to_device(a), to_device(v)
+    pdq.pdq_sort_pairs(dk[lo:end], dv[lo:end], key_dtype=CODE[np.dtype(dtype)])
+    torch.cuda.synchronize()
+    gk, gv = to_host(dk, dtype), to_host(dv, v.dtype).astype(np.int64)
+    assert np.array_equal(gk, want)
+    assert np.array_equal(a[gv], gk)  # every key kept its value (untouched outside the slice)
+
+
+def test_nearly_sorted_huge_segment():
+    """A segment above the persistent kernel's limit takes the plain path, fix-up included."""
+    from gpu_helpers import gpu_sort_segmented
+    big = (1 << 20) + 77
+    a = np.concatenate([workloads.pattern("asc_swaps", big, workloads.config_seed(83), dtype=np.int64),
+                        workloads.uniform_bits(5000, np.int64, workloads.config_seed(84))]).astype(np.int32)
+    offs = np.array([0, big, big + 5000], dtype=np.int64)
+    got, _, _, rc = gpu_sort_segmented(a, offs)
+    assert rc == 0
+    want = np.concatenate([np.sort(a[:big]), np.sort(a[big:])])
+    assert np.array_equal(got, want)
