@@ -60,18 +60,24 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-// Exclusive scan of nbins counters held in shared memory `in`, result in `out` (may alias).
-// Returns the total in *total (shared).  All threads of the block must call it.
-template <int THREADS>
+// Identity placement of counters in shared memory.
+struct SlotIdentity {
+  __device__ __forceinline__ int operator()(int b) const { return b; }
+};
+
+// Exclusive scan of nbins counters held in shared memory `in`, result in `out` (may alias);
+// counter b lives at in[slot(b)] and its prefix goes to out[slot(b)].  All threads of the block
+// must call it.
+template <int THREADS, class Slot = SlotIdentity>
 __device__ void block_exclusive_scan(const uint32_t* in, uint32_t* out, int nbins,
-                                     uint32_t* warp_tmp /* >= THREADS/32 + 1 */) {
+                                     uint32_t* warp_tmp /* >= THREADS/32 + 1 */, Slot slot = Slot()) {
   const int tid = threadIdx.x;
   const int per = (nbins + THREADS - 1) / THREADS;
   const int lo = tid * per;
   uint32_t sum = 0;
   for (int i = 0; i < per; ++i) {
     const int b = lo + i;
-    if (b < nbins) sum += in[b];
+    if (b < nbins) sum += in[slot(b)];
   }
   // inclusive scan of per-thread sums across the block
   const int lane = tid & 31, warp = tid >> 5;
@@ -99,8 +105,8 @@ __device__ void block_exclusive_scan(const uint32_t* in, uint32_t* out, int nbin
   for (int i = 0; i < per; ++i) {
     const int b = lo + i;
     if (b < nbins) {
-      const uint32_t c = in[b];
-      out[b] = run;
+      const uint32_t c = in[slot(b)];
+      out[slot(b)] = run;
       run += c;
     }
   }
@@ -200,18 +206,7 @@ __global__ void reverse_kernel(T* __restrict__ a, int64_t n) {
 // Eytzinger tree over the B-1 sorted splitters: tree[1..B-1], node j has children 2j and 2j+1.
 // Descent "go right when code > node" ends at leaf B + b where b = #splitters < code.  The key
 // then belongs to bin 2b+1 if it equals splitter b (an equality bucket, Sec. 3), else bin 2b.
-template <class U>
-__device__ __forceinline__ int classify(U code, const U* __restrict__ tree,
-                                        const U* __restrict__ spl, int logb) {
-  int j = 1;
-  for (int l = 0; l < logb; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
-  const int B = 1 << logb;
-  const int b = j - B;
-  const int sb = b < B - 1 ? b : B - 2;
-  return 2 * b + (code == spl[sb] ? 1 : 0);
-}
-
-// Same, with the depth known at compile time (fully unrolled descent).
+// The depth is known at compile time (fully unrolled descent).
 template <int LOGB, class U>
 __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, const U* __restrict__ spl) {
   int j = 1;
@@ -224,30 +219,26 @@ __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, co
 }
 
 // Exact rank prefilter over the splitter range [lo, hi] = [spl[0], spl[B-2]]: entry k of `tab`
-// covers the codes lo + [k << shift, (k + 1) << shift) and stores (b_lo | b_hi << 16) with
-// b_lo = #splitters < first code and b_hi = #splitters <= last code of the slice, so every
-// code of the slice has rank (#splitters < code) in [b_lo, b_hi].  Codes outside [lo, hi] are
-// clamped into the first or last slice, whose bounds still hold for them.
-// When b_hi <= b_lo + 1 the entry's candidate s0 = spl[b_lo] settles both the rank
-// (b_lo + [s0 < code]) and the equality test (code == s0): splitter b_lo + 1, if any, lies above
-// the slice and so cannot equal a code in it.
-// Table size per key width: 2048 entries of 8 bytes (4-byte codes) or 1024 of 16 bytes.
+// covers the codes lo + [k << shift, (k + 1) << shift) and holds the 32-bit word
+// (b_lo | b_hi << 16) with b_lo = #splitters < first code and b_hi = #splitters <= last code of
+// the slice, so every code of the slice has rank (#splitters < code) in [b_lo, b_hi].  Codes
+// outside [lo, hi] are clamped into the first or last slice, whose bounds still hold for them.
+// When b_hi <= b_lo + 1 the only candidate is s0 = spl[b_lo] (present when b_lo < b_hi): it
+// settles both the rank (b_lo + [s0 < code]) and the equality test (code == s0), as splitter
+// b_lo + 1, if any, lies above the slice and cannot equal a code in it.  Only lanes whose slice
+// holds a candidate read spl, so most lookups cost one 4-byte shared load.
+// 4096 entries of 4 bytes (16 KB) for both key widths.
 template <class U>
-__host__ __device__ constexpr int pref_bits() { return sizeof(U) == 4 ? 11 : 10; }
+__host__ __device__ constexpr int pref_bits() { return 12; }
 template <class U>
 __host__ __device__ constexpr int pref_entries() { return 1 << pref_bits<U>(); }
 
-// One slice: rank bounds (b_lo | b_hi << 16) and the slice's candidate splitter
-// s0 = spl[min(b_lo, B - 2)], the only splitter a code of a one-candidate slice is compared with.
-template <class U>
-struct alignas(2 * sizeof(U)) PrefEnt {
-  U range;
-  U s0;
-};
+// One slice: its rank bounds, b_lo | b_hi << 16.
+using PrefEnt = uint32_t;
 // Bytes of one task's prefilter table, the same for both key widths.
 constexpr size_t kPrefTableBytes = 16384;
-static_assert(pref_entries<uint32_t>() * sizeof(PrefEnt<uint32_t>) == kPrefTableBytes &&
-                  pref_entries<uint64_t>() * sizeof(PrefEnt<uint64_t>) == kPrefTableBytes,
+static_assert(pref_entries<uint32_t>() * sizeof(PrefEnt) == kPrefTableBytes &&
+                  pref_entries<uint64_t>() * sizeof(PrefEnt) == kPrefTableBytes,
               "prefilter table size");
 
 template <class U>
@@ -257,65 +248,79 @@ struct Pref {
   int nent;
 };
 
-// Bin of a code: a prefilter slice with at most one candidate splitter settles the rank with
-// one predicated comparison (branch-free); a wider slice falls back to the Eytzinger descent.
+// Histogram slot of a code: rank b (#splitters < code) for a key inside bucket b, B + b for a key
+// equal to splitter b (its equality bin).  The slot is the bin's place in the per-CTA shared
+// histograms (BinSlot below: bin 2b at slot b, bin 2b+1 at slot B + b).  A prefilter slice with
+// at most one candidate splitter settles it with one predicated comparison (branch-free); a
+// wider slice falls back to the Eytzinger descent.
 template <int LOGB, class U>
 __device__ __forceinline__ int classify_fast(U code, const U* __restrict__ tree, const U* __restrict__ spl,
-                                             const PrefEnt<U>* __restrict__ tab, const Pref<U>& pf) {
+                                             const PrefEnt* __restrict__ tab, const Pref<U>& pf) {
   constexpr int B = 1 << LOGB;
   const U y = code < pf.lo ? pf.lo : (code > pf.hi ? pf.hi : code);
-  const PrefEnt<U> e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
-  const int blo = (int)(e.range & 0xFFFFu), bhi = (int)((e.range >> 16) & 0xFFFFu);
+  const uint32_t e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
+  const int blo = (int)(e & 0xFFFFu), bhi = (int)(e >> 16);
   if (bhi - blo <= 1) {
     const bool cand = blo < bhi;
-    return 2 * (blo + ((cand && e.s0 < code) ? 1 : 0)) + ((cand && code == e.s0) ? 1 : 0);
+    U s0 = U(0);
+    if (cand) s0 = spl[blo];
+    return blo + ((cand && s0 < code) ? 1 : 0) + ((cand && code == s0) ? B : 0);
   }
   int j = 1;
 #pragma unroll
   for (int l = 0; l < LOGB; ++l) j = 2 * j + (code > tree[j] ? 1 : 0);
   const int b = j - B;
   const int sb = b < B - 1 ? b : B - 2;
-  return 2 * b + (code == spl[sb] ? 1 : 0);
+  return b + (code == spl[sb] ? B : 0);
 }
 
-// Splitter classifier of a task with 2^LOGB buckets: one code at a time, or N codes at once
-// (all prefilter lookups, then all single-candidate refinements, so the N dependency chains of
-// shared loads overlap; the tree runs only when some code's slice holds several candidates).
+// Splitter classifier of a task with 2^LOGB buckets (returns histogram slots, see
+// classify_fast): one code at a time, or N codes at once
+// (all prefilter lookups, then all candidate-splitter loads, then the comparisons, so the N
+// dependency chains of shared loads overlap; the tree runs only when some code's slice holds
+// several candidates).
 template <int LOGB, class U>
 struct SplitterClassifier {
   const U* tree;
   const U* spl;
-  const PrefEnt<U>* tab;
+  const PrefEnt* tab;
   Pref<U> pf;
   __device__ __forceinline__ int operator()(U code) const { return classify_fast<LOGB>(code, tree, spl, tab, pf); }
   template <int N>
-  __device__ __forceinline__ void vec(const U (&code)[N], int (&bin)[N]) const {
+  __device__ __forceinline__ void vec(const U (&code)[N], int (&slot)[N]) const {
     constexpr int B = 1 << LOGB;
-    PrefEnt<U> e[N];
+    uint32_t e[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
       const U y = code[i] < pf.lo ? pf.lo : (code[i] > pf.hi ? pf.hi : code[i]);
       e[i] = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
     }
+    U s0[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {  // candidate splitters, read only where the slice has one
+      const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
+      s0[i] = U(0);
+      if (blo < bhi) s0[i] = spl[blo];
+    }
     bool wide = false;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const int blo = (int)(e[i].range & 0xFFFFu), bhi = (int)((e[i].range >> 16) & 0xFFFFu);
+      const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
       const bool cand = blo < bhi;
-      bin[i] = 2 * (blo + ((cand && e[i].s0 < code[i]) ? 1 : 0)) + ((cand && code[i] == e[i].s0) ? 1 : 0);
+      slot[i] = blo + ((cand && s0[i] < code[i]) ? 1 : 0) + ((cand && code[i] == s0[i]) ? B : 0);
       wide |= bhi - blo > 1;
     }
     if (wide) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const int blo = (int)(e[i].range & 0xFFFFu), bhi = (int)((e[i].range >> 16) & 0xFFFFu);
+        const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
         if (bhi - blo > 1) {
           int j = 1;
 #pragma unroll
           for (int l = 0; l < LOGB; ++l) j = 2 * j + (code[i] > tree[j] ? 1 : 0);
           const int b = j - B;
           const int sb = b < B - 1 ? b : B - 2;
-          bin[i] = 2 * b + (code[i] == spl[sb] ? 1 : 0);
+          slot[i] = b + (code[i] == spl[sb] ? B : 0);
         }
       }
     }
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(THREADS)
 sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_logb, int oversample,
               const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
               typename Key<KT>::U* __restrict__ tree_out, typename Key<KT>::U* __restrict__ spl_out,
-              Pref<typename Key<KT>::U>* __restrict__ pref_out, PrefEnt<typename Key<KT>::U>* __restrict__ tab_out) {
+              Pref<typename Key<KT>::U>* __restrict__ pref_out, PrefEnt* __restrict__ tab_out) {
   using U = typename Key<KT>::U;
   __shared__ U s[kMaxSamples];
   const Task t = tasks[blockIdx.x];
@@ -367,14 +372,26 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
   const U* src = (t.buf == kBufKeys ? keys : tmp) + t.begin;
   const uint64_t seed = mix64((uint64_t)t.begin * 0x9E3779B97F4A7C15ull ^ mix64((uint64_t)t.size) ^
                               ((uint64_t)t.attempt << 48));
-  for (int j = threadIdx.x; j < ns; j += THREADS) {
-    const uint64_t r = mix64(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull);
-    const int64_t pos = (int64_t)(r % (uint64_t)t.size);
-    const U x = src[pos];
-    s[j] = t.enc ? x : Key<KT>::enc(x);
+  constexpr int PER = (kMaxSamples + THREADS - 1) / THREADS;
+  U xs[PER];  // all of a thread's sample loads in flight at once
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int j = threadIdx.x + r * THREADS;
+    xs[r] = U(0);
+    if (j < ns) {
+      const uint64_t h = mix64(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull);
+      xs[r] = src[(int64_t)(h % (uint64_t)t.size)];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int j = threadIdx.x + r * THREADS;
+    if (j < ns) s[j] = t.enc ? xs[r] : Key<KT>::enc(xs[r]);
   }
   __syncthreads();
-  // bitonic sort of s[0..ns), ns a power of two
+  // bitonic sort of s[0..ns), ns a power of two.  A layer of distance j <= 32 pairs elements of
+  // one aligned 64-element block, and a warp's 32 consecutive q cover exactly such blocks, so
+  // between two such layers a warp barrier suffices.
   for (int k = 2; k <= ns; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
       for (int q = threadIdx.x; q < ns / 2; q += THREADS) {
@@ -384,9 +401,11 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
         const U a = s[i], b = s[l];
         if ((a > b) == up) { s[i] = b; s[l] = a; }
       }
-      __syncthreads();
+      const int jn = j > 1 ? j >> 1 : k;  // distance of the next layer
+      if (j <= 32 && jn <= 32) __syncwarp(); else __syncthreads();
     }
   }
+  __syncthreads();
   U* tree = tree_out + (size_t)blockIdx.x * kBMax;
   U* spl = spl_out + (size_t)blockIdx.x * kBMax;
   const int step = ns / B;
@@ -406,7 +425,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
     pf.nent = nent;
     pref_out[blockIdx.x] = pf;
   }
-  PrefEnt<U>* tab = tab_out + (size_t)blockIdx.x * pref_entries<U>();
+  PrefEnt* tab = tab_out + (size_t)blockIdx.x * pref_entries<U>();
   for (int k = threadIdx.x; k < nent; k += THREADS) {
     const U first = lo + ((U)k << shift);
     const U last = k == nent - 1 ? hi : first + (((U)1 << shift) - 1);
@@ -420,10 +439,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
       const int m = (a2 + c2) >> 1;
       if (s[(m + 1) * step - 1] <= last) a2 = m + 1; else c2 = m;
     }
-    PrefEnt<U> ent;
-    ent.range = (U)((uint32_t)a | ((uint32_t)a2 << 16));
-    ent.s0 = s[((a < B - 2 ? a : B - 2) + 1) * step - 1];
-    tab[k] = ent;
+    tab[k] = (uint32_t)a | ((uint32_t)a2 << 16);
   }
 }
 
@@ -450,11 +466,11 @@ struct SplitterCls {
     const U* tree;
     const U* spl;
     const Pref<U>* pref;
-    const PrefEnt<U>* tab;
+    const PrefEnt* tab;
   };
   struct Shared {
     U tree[kBMax], spl[kBMax];
-    PrefEnt<U> tab[pref_entries<U>()];
+    PrefEnt tab[pref_entries<U>()];
     Pref<U> pf;
     int logb;
   };
@@ -482,6 +498,19 @@ struct SplitterCls {
   }
 };
 
+// Shared-memory slot of a bin in the per-CTA histograms.  With equality bins nearly every key
+// of distinct data lands in an even bin (2b), so an identity layout would leave the odd banks
+// idle and double the bank conflicts of the histogram atomics and lookups; bucket bin 2b lives
+// at slot b and equality bin 2b+1 at slot B + b instead.  Without equality bins: identity.
+// Classifiers return slots; this map serves the loops that walk the bins in key order.
+template <bool EQ>
+struct BinSlot {
+  int lb;  // log2 of the bucket count B = nbins / 2 (EQ only)
+  __device__ __forceinline__ int operator()(int bin) const { return EQ ? (bin >> 1) | ((bin & 1) << lb) : bin; }
+  // the slot holds an equality bin
+  __device__ __forceinline__ bool equal(int sl) const { return EQ && (sl >> lb) != 0; }
+};
+
 // ================================================================== count
 // One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE codes that stream
 // into STAGES shared buffers by bulk copy; elements of a window outside the chunk are masked
@@ -507,6 +536,7 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
   const int nb = CLS::setup(cs, cp, c.task);
+  const BinSlot<CLS::kEqualBins> slot{__ffs(nb) - 2};
   for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&bars[i], 1);
@@ -552,10 +582,10 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 #pragma unroll
             for (int i = 0; i < VEC; ++i) v[i] = Key<KT>::enc(v[i]);
           }
-          int bin[VEC];
-          classify.vec(v, bin);
+          int sl[VEC];
+          classify.vec(v, sl);
 #pragma unroll
-          for (int i = 0; i < VEC; ++i) atomicAdd(&hist[bin[i]], 1u);
+          for (int i = 0; i < VEC; ++i) atomicAdd(&hist[sl[i]], 1u);
         }
       } else {
         const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(wa - ws);
@@ -592,7 +622,7 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   }
   __syncthreads();
   uint32_t* out = counts + (size_t)blockIdx.x * bin_stride;
-  for (int b = threadIdx.x; b < nb; b += THREADS) out[b] = hist[b];
+  for (int b = threadIdx.x; b < nb; b += THREADS) out[b] = hist[slot(b)];
 }
 
 // ================================================================== scan
@@ -728,8 +758,9 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
   const int nb = CLS::setup(cs, cp, c.task);
+  const BinSlot<CLS::kEqualBins> slot{__ffs(nb) - 2};  // hist, cursor, gbase and stage_b hold slots
   for (int b = threadIdx.x; b < nb; b += THREADS) {
-    cursor[b] = offsets[(size_t)blockIdx.x * bin_stride + b];
+    cursor[slot(b)] = offsets[(size_t)blockIdx.x * bin_stride + b];
     hist[b] = 0;
   }
   if (threadIdx.x == 0) {
@@ -805,7 +836,7 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 
       U code[ITEMS];
       V val[ITEMS];
-      uint32_t packed[ITEMS];  // bin << 16 | rank inside the bin; 0xFFFFFFFF for masked slots
+      uint32_t packed[ITEMS];  // slot << 16 | rank inside the bin; 0xFFFFFFFF for masked elements
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const int vi = threadIdx.x + q * THREADS;
@@ -818,18 +849,17 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
           if (VB) val[q * VK + i] = bv[vi * VK + i];
         }
         if (full) {  // interior window: classify the vector at once, no masks
-          int bin[VK];
-          classify.vec(v, bin);
+          int sl[VK];
+          classify.vec(v, sl);
 #pragma unroll
-          for (int i = 0; i < VK; ++i)
-            packed[q * VK + i] = ((uint32_t)bin[i] << 16) | atomicAdd(&hist[bin[i]], 1u);
+          for (int i = 0; i < VK; ++i) packed[q * VK + i] = ((uint32_t)sl[i] << 16) | atomicAdd(&hist[sl[i]], 1u);
         } else {
 #pragma unroll
           for (int i = 0; i < VK; ++i) {
             const int k = vi * VK + i;
             if (k >= k0 && k < k1) {
-              const int bin = classify(v[i]);
-              packed[q * VK + i] = ((uint32_t)bin << 16) | atomicAdd(&hist[bin], 1u);
+              const int sl = classify(v[i]);
+              packed[q * VK + i] = ((uint32_t)sl << 16) | atomicAdd(&hist[sl], 1u);
             } else {
               packed[q * VK + i] = 0xFFFFFFFFu;
             }
@@ -837,21 +867,23 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         }
       }
       __syncthreads();
-      block_exclusive_scan<THREADS>(hist, hist, nb, wtmp);  // hist := window start of each bin
+      block_exclusive_scan<THREADS>(hist, hist, nb, wtmp, slot);  // hist := window start of each bin
       for (int b = threadIdx.x; b < nb; b += THREADS) {
-        const uint32_t next = (b + 1 < nb) ? hist[b + 1] : (uint32_t)cnt;
-        gbase[b] = cursor[b] - hist[b];
-        cursor[b] += next - hist[b];
+        const int sl = slot(b);
+        const uint32_t start = hist[sl];
+        const uint32_t next = (b + 1 < nb) ? hist[slot(b + 1)] : (uint32_t)cnt;
+        gbase[sl] = cursor[sl] - start;
+        cursor[sl] += next - start;
       }
       // stage in place: every thread has read its codes from the buffer (scan barriers above)
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
         if (packed[e] != 0xFFFFFFFFu) {
-          const uint32_t bin = packed[e] >> 16;
-          const uint32_t p = hist[bin] + (packed[e] & 0xFFFFu);
+          const uint32_t sl = packed[e] >> 16;
+          const uint32_t p = hist[sl] + (packed[e] & 0xFFFFu);
           bk[p] = code[e];
           if (VB) bv[p] = val[e];
-          stage_b[p] = (uint16_t)bin;
+          stage_b[p] = (uint16_t)sl;
         }
       }
       __syncthreads();
@@ -859,7 +891,7 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
         const int b = stage_b[i];
         const uint32_t o = gbase[b] + (uint32_t)i;
         const U k = bk[i];
-        dstk[o] = (CLS::kEqualBins && dst_is_keys && (b & 1)) ? Key<KT>::dec(k) : k;  // equality bin: final
+        dstk[o] = (dst_is_keys && slot.equal(b)) ? Key<KT>::dec(k) : k;  // equality bin: final
         if (VB) dstv[o] = bv[i];
       };
       if (full) {
@@ -880,6 +912,27 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 }
 
 // ================================================================== bookkeeping (Sec. 4.1, Sec. 3)
+// One thread per child bin.  Every warp stays whole until its counters are updated: list slots
+// and counter increments are aggregated per warp (one atomic per warp and list), because at
+// the second level tens of thousands of children hit the same few counters.
+// Reserves `want`-many slots of a list for the lanes that want one; returns the lane's slot.
+__device__ __forceinline__ unsigned long long warp_reserve(bool want, unsigned long long* counter) {
+  const unsigned m = __ballot_sync(0xffffffffu, want);
+  if (m == 0u) return 0ull;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0ull;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+}
+
+// Adds the warp's sum of v to *counter (one atomic per warp, none when the sum is zero).
+__device__ __forceinline__ void warp_add(unsigned long long v, unsigned long long* counter) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
+}
+
 static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_nbins,
                                 const uint2* __restrict__ children, int bin_stride, int equal_bins,
                                 int base_cap, Counters* ctr,
@@ -889,9 +942,7 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   const int task = blockIdx.y;
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   const int nb = task_nbins[task];
-  if (b >= nb) return;
-  const uint2 ch = children[(size_t)task * bin_stride + b];
-  if (ch.y == 0) return;
+  const uint2 ch = b < nb ? children[(size_t)task * bin_stride + b] : make_uint2(0u, 0u);
   const Task t = tasks[task];
   const int dst = t.buf == kBufKeys ? kBufTmp : kBufKeys;
   Item it;
@@ -899,43 +950,47 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   it.size = ch.y;
   it.buf = (uint16_t)dst;
   it.enc = 1;
-  auto push = [&](Item* list, unsigned long long* counter, int64_t cap) {
-    const unsigned long long k = atomicAdd(counter, 1ull);
-    if ((int64_t)k < cap) list[k] = it;
-    else atomicAdd(&ctr->overflow, 1ull);
-  };
-  if (equal_bins && (b & 1)) {  // equality bucket: every key equals the splitter, final (Sec. 3)
-    atomicAdd(&ctr->equal_buckets, 1ull);
-    if (dst == kBufTmp) {
-      push(copy_items, &ctr->n_copy, caps.copy_cap);
-      atomicAdd(&ctr->copy_elems, (unsigned long long)ch.y);
-    }
-    return;
-  }
-  if ((int64_t)ch.y <= base_cap) {
-    const int cls = ch.y <= 1024u ? 0 : (ch.y <= 2048u ? 1 : (ch.y <= 4096u ? 2 : (ch.y <= 8192u ? 3 : 4)));
-    push(base_items + caps.base_off[cls], &ctr->n_base[cls], caps.base_cap[cls]);
-    atomicAdd(&ctr->base_elems, (unsigned long long)ch.y);
-    return;
-  }
+  // what becomes of this child
+  const bool live = ch.y != 0u;
+  const bool equal = live && equal_bins && (b & 1);  // every key equals the splitter: final (Sec. 3)
+  const bool base = live && !equal && (int64_t)ch.y <= base_cap;
+  const bool split = live && !equal && !base;
   // bad split: the child kept more than 7/8 of its parent (p = 1/8, a shift; Sec. 4.1)
-  const bool bad = (int64_t)ch.y > t.size - (t.size >> 3);
-  if (bad) atomicAdd(&ctr->bad_splits, 1ull);
+  const bool bad = split && (int64_t)ch.y > t.size - (t.size >> 3);
   const int left = t.bad_left - (bad ? 1 : 0);
-  if (left <= 0) {
-    push(fb_items, &ctr->n_fallback, caps.fb_cap);
-    return;
+  const bool fallback = split && left <= 0;
+  const bool recurse = split && left > 0;
+  const bool copy = equal && dst == kBufTmp;
+  const int cls = ch.y <= 1024u ? 0 : (ch.y <= 2048u ? 1 : (ch.y <= 4096u ? 2 : (ch.y <= 8192u ? 3 : 4)));
+
+  warp_add(equal ? 1ull : 0ull, &ctr->equal_buckets);
+  warp_add(bad ? 1ull : 0ull, &ctr->bad_splits);
+  warp_add(copy ? (unsigned long long)ch.y : 0ull, &ctr->copy_elems);
+  warp_add(base ? (unsigned long long)ch.y : 0ull, &ctr->base_elems);
+  auto put = [&](bool want, Item* list, unsigned long long* counter, int64_t cap) {
+    const unsigned long long k = warp_reserve(want, counter);
+    if (want) {
+      if ((int64_t)k < cap) list[k] = it;
+      else atomicAdd(&ctr->overflow, 1ull);
+    }
+  };
+  put(copy, copy_items, &ctr->n_copy, caps.copy_cap);
+#pragma unroll
+  for (int c = 0; c < kBaseClasses; ++c)
+    put(base && cls == c, base_items + caps.base_off[c], &ctr->n_base[c], caps.base_cap[c]);
+  put(fallback, fb_items, &ctr->n_fallback, caps.fb_cap);
+  const unsigned long long k = warp_reserve(recurse, &ctr->n_next);
+  if (recurse) {
+    Task nt;
+    nt.begin = it.begin;
+    nt.size = it.size;
+    nt.buf = dst;
+    nt.enc = 1;
+    nt.bad_left = left;
+    nt.attempt = t.attempt + 1;
+    if ((int64_t)k < caps.task_cap) next[k] = nt;
+    else atomicAdd(&ctr->overflow, 1ull);
   }
-  Task nt;
-  nt.begin = it.begin;
-  nt.size = it.size;
-  nt.buf = dst;
-  nt.enc = 1;
-  nt.bad_left = left;
-  nt.attempt = t.attempt + 1;
-  const unsigned long long k = atomicAdd(&ctr->n_next, 1ull);
-  if ((int64_t)k < caps.task_cap) next[k] = nt;
-  else atomicAdd(&ctr->overflow, 1ull);
 }
 
 // ================================================================== base sort (Sec. 5.1)
@@ -1202,16 +1257,72 @@ constexpr size_t base_sort_smem() {
 }
 
 // ================================================================== copy temp -> keys (decode)
-template <int KT, int VB>
-__global__ void copy_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict__ keys,
-                            typename Val<VB>::T* __restrict__ vals, const typename Key<KT>::U* __restrict__ tmpk,
-                            const typename Val<VB>::T* __restrict__ tmpv) {
-  const Item it = items[blockIdx.x];
-  for (int64_t i = (int64_t)blockIdx.y * blockDim.x + threadIdx.x; i < it.size;
-       i += (int64_t)gridDim.y * blockDim.x) {
-    const int64_t p = it.begin + i;
-    keys[p] = Key<KT>::dec(tmpk[p]);
-    if (VB) vals[p] = tmpv[p];
+// Final buckets left in the temp buffer (equality buckets of odd levels) go home, decoded.  Their
+// sizes are skewed (one duplicated value can hold most of the array), so the work is cut into
+// tiles of TILE elements over all items: copy_plan_kernel numbers the tiles (one CTA; tile0[k] =
+// first tile of item k, tile0[n] = total), and every CTA of copy_kernel takes tiles grid-strided.
+template <int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS)
+copy_plan_kernel(const Item* __restrict__ items, int n, uint32_t* __restrict__ tile0) {
+  __shared__ uint32_t wtmp[THREADS / 32 + 1];
+  const int tid = threadIdx.x;
+  const int per = (n + THREADS - 1) / THREADS;
+  const int lo = tid * per;
+  uint32_t sum = 0;
+  for (int i = 0; i < per && lo + i < n; ++i) sum += (items[lo + i].size + TILE - 1) / TILE;
+  const int lane = tid & 31, warp = tid >> 5;
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    constexpr int NW = THREADS / 32;
+    uint32_t w = lane < NW ? wtmp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NW) wtmp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = x - sum + (warp > 0 ? wtmp[warp - 1] : 0u);
+  for (int i = 0; i < per && lo + i < n; ++i) {
+    tile0[lo + i] = run;
+    run += (items[lo + i].size + TILE - 1) / TILE;
+  }
+  if (tid == THREADS - 1) tile0[n] = run;
+}
+
+template <int KT, int VB, int THREADS, int TILE>
+__global__ void __launch_bounds__(THREADS)
+copy_kernel(const Item* __restrict__ items, int n, const uint32_t* __restrict__ tile0,
+            typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
+            const typename Key<KT>::U* __restrict__ tmpk, const typename Val<VB>::T* __restrict__ tmpv) {
+  static_assert(TILE % THREADS == 0, "tile shape");
+  const uint32_t total = tile0[n];
+  for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+    int a = 0, b = n - 1;  // the item holding tile t: last k with tile0[k] <= t
+    while (a < b) {
+      const int m = (a + b + 1) >> 1;
+      if (tile0[m] <= t) a = m; else b = m - 1;
+    }
+    const Item it = items[a];
+    const int64_t e0 = (int64_t)(t - tile0[a]) * TILE;
+    const int64_t len = (int64_t)it.size - e0 < TILE ? (int64_t)it.size - e0 : TILE;
+    const int64_t base = it.begin + e0;
+#pragma unroll 8
+    for (int r = 0; r < TILE / THREADS; ++r) {
+      const int i = r * THREADS + threadIdx.x;
+      if (i < len) {
+        keys[base + i] = Key<KT>::dec(tmpk[base + i]);
+        if (VB) vals[base + i] = tmpv[base + i];
+      }
+    }
   }
 }
 

@@ -26,6 +26,7 @@ constexpr float kTrainLr = 0.05f;
 
 constexpr int64_t kFixMin = int64_t(1) << 16;  // smallest array given the nearly-sorted fix-up
 constexpr int kFixTile = 8192;                 // elements per tile of the fix-up's peel pass
+constexpr int kCopyTile = 8192;                // elements per tile of the copy of final buckets home
 
 inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool fixup = true) {
   Layout L;
@@ -160,7 +161,7 @@ class PlainSorter {
     spl_ = reinterpret_cast<U*>(ws + L_.spl);
     children_ = reinterpret_cast<uint2*>(ws + L_.children);
     pref_ = reinterpret_cast<Pref<U>*>(ws + L_.pref);
-    tab_ = reinterpret_cast<PrefEnt<U>*>(ws + L_.tab);
+    tab_ = reinterpret_cast<PrefEnt*>(ws + L_.tab);
     base_items_ = reinterpret_cast<Item*>(ws + L_.base_items);
     copy_items_ = reinterpret_cast<Item*>(ws + L_.copy_items);
     fb_items_ = reinterpret_cast<Item*>(ws + L_.fb_items);
@@ -219,7 +220,7 @@ class PlainSorter {
   uint32_t* counts_;
   uint2* children_;
   Pref<U>* pref_;
-  PrefEnt<U>* tab_;
+  PrefEnt* tab_;
   Item *base_items_, *copy_items_, *fb_items_;
   cudaStream_t st_;
 
@@ -730,9 +731,14 @@ class PlainSorter {
       base_elems = 0;
     }
     if (h.n_copy) {
+      // the tile numbering lives in the counts region, free between a level's scatter and the
+      // next level's count (item_cap + 1 words always fit: it holds at least 4096 bytes per task)
       LaunchScope ls("copy", st_, 2.0 * (double)h.copy_elems * (KS + VB));
-      dim3 grid((unsigned)h.n_copy, 16);
-      copy_kernel<KT, VB><<<grid, 256, 0, st_>>>(copy_items_, keys_, vals_, tmpk_, tmpv_);
+      uint32_t* tile0 = counts_;
+      copy_plan_kernel<1024, kCopyTile><<<1, 1024, 0, st_>>>(copy_items_, (int)h.n_copy, tile0);
+      copy_kernel<KT, VB, 256, kCopyTile><<<(unsigned)(a_.num_sms * 8), 256, 0, st_>>>(
+          copy_items_, (int)h.n_copy, tile0, keys_, vals_, tmpk_, tmpv_);
+      note_launch_count(1);
     }
     PDQ_LAUNCHED("copy");
     if (h.n_fallback) {
