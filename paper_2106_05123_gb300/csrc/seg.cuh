@@ -208,6 +208,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
   }
   const int B = 1 << logb;
   const int nb = 2 * B;
+  const BinSlot<true> slot{logb};  // hist, curs and th are indexed by bin slot (bank spread)
   int ns = prm.oversample * B;
   if (ns > kMaxSamples) ns = kMaxSamples;
   if (ns < B) ns = B;
@@ -276,7 +277,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
         const int j = e * THREADS + tid;
         if (t0 + j < size) {
           const U x = kb[j];
-          atomicAdd(&hist[classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl)], 1u);
+          atomicAdd(&hist[slot(classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl))], 1u);
         }
       }
       __syncthreads();
@@ -284,7 +285,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
     cp_async_wait<0>();
   });
   __syncthreads();
-  block_exclusive_scan<THREADS>(hist, curs, nb, wtmp);  // curs := bin starts
+  block_exclusive_scan<THREADS>(hist, curs, nb, wtmp, slot);  // curs := bin starts
   // scatter, one tile at a time: rank inside the tile per bin, stage grouped by bin in shared
   // memory, then write each bin's run of the tile at its cursor (contiguous stores); equality
   // bins written to the key buffer are final, so they are decoded on the way
@@ -302,19 +303,19 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
       __syncthreads();
       const U* kb = kslot + (k & 1) * T;
       const V* vb = vslot + (k & 1) * T;
-      int bin[ITP];
+      int bin[ITP];  // bin slots
       uint32_t rk[ITP];
 #pragma unroll
       for (int e = 0; e < ITP; ++e) {
         const int j = e * THREADS + tid;
         if (j < cnt) {
           const U x = kb[j];
-          bin[e] = classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl);
+          bin[e] = slot(classify_t<LL>(enc ? x : Key<KT>::enc(x), s_tree, s_spl));
           rk[e] = atomicAdd(&th[bin[e]], 1u);
         }
       }
       __syncthreads();
-      block_exclusive_scan<THREADS>(th, th, nb, wtmp);  // th := tile starts
+      block_exclusive_scan<THREADS>(th, th, nb, wtmp, slot);  // th := tile starts
 #pragma unroll
       for (int e = 0; e < ITP; ++e) {
         const int j = e * THREADS + tid;
@@ -322,7 +323,7 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
           const U x = kb[j];
           const U code = enc ? x : Key<KT>::enc(x);
           const uint32_t p = th[bin[e]] + rk[e];
-          sk[p] = (dst_is_keys && (bin[e] & 1)) ? Key<KT>::dec(code) : code;
+          sk[p] = (dst_is_keys && slot.equal(bin[e])) ? Key<KT>::dec(code) : code;
           sb[p] = (uint16_t)bin[e];
           if (VB) sv[p] = vb[j];
         }
@@ -335,7 +336,10 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
         if (VB) dstv[g] = sv[j];
       }
       __syncthreads();
-      for (int b = tid; b < nb; b += THREADS) curs[b] += (b + 1 < nb ? th[b + 1] : (uint32_t)cnt) - th[b];
+      for (int b = tid; b < nb; b += THREADS) {
+        const int sl = slot(b);
+        curs[sl] += (b + 1 < nb ? th[slot(b + 1)] : (uint32_t)cnt) - th[sl];
+      }
       __syncthreads();
     }
     cp_async_wait<0>();
@@ -343,9 +347,9 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
   __syncthreads();
   // children
   for (int b = tid; b < nb; b += THREADS) {
-    const uint32_t cnt = hist[b];
+    const uint32_t cnt = hist[slot(b)];
     if (cnt == 0) continue;
-    const uint32_t start = curs[b] - cnt;
+    const uint32_t start = curs[slot(b)] - cnt;
     Item it{t.begin + start, cnt, (uint16_t)(from_keys ? kBufTmp : kBufKeys), 1};
     if (b & 1) {
       atomicAdd(&st->equal_buckets, 1ull);
@@ -378,9 +382,9 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
   // equality buckets left in the temp buffer go home now, decoded
   if (!dst_is_keys) {
     for (int b = 1; b < nb; b += 2) {
-      const uint32_t cnt = hist[b];
+      const uint32_t cnt = hist[slot(b)];
       if (cnt == 0) continue;
-      const int64_t start = curs[b] - cnt;
+      const int64_t start = curs[slot(b)] - cnt;
       for (int64_t i = tid; i < cnt; i += THREADS) {
         keys[t.begin + start + i] = Key<KT>::dec(tmpk[t.begin + start + i]);
         if (VB) vals[t.begin + start + i] = tmpv[t.begin + start + i];
