@@ -219,22 +219,24 @@ __device__ __forceinline__ int classify_t(U code, const U* __restrict__ tree, co
 }
 
 // Exact rank prefilter over the splitter range [lo, hi] = [spl[0], spl[B-2]]: entry k of `tab`
-// covers the codes lo + [k << shift, (k + 1) << shift) and holds the 32-bit word
-// (b_lo | b_hi << 16) with b_lo = #splitters < first code and b_hi = #splitters <= last code of
-// the slice, so every code of the slice has rank (#splitters < code) in [b_lo, b_hi].  Codes
-// outside [lo, hi] are clamped into the first or last slice, whose bounds still hold for them.
-// When b_hi <= b_lo + 1 the only candidate is s0 = spl[b_lo] (present when b_lo < b_hi): it
-// settles both the rank (b_lo + [s0 < code]) and the equality test (code == s0), as splitter
-// b_lo + 1, if any, lies above the slice and cannot equal a code in it.  Only lanes whose slice
-// holds a candidate read spl, so most lookups cost one 4-byte shared load.
+// covers the codes lo + [k << shift, (k + 1) << shift).  With b_lo = #splitters < first code and
+// b_hi = #splitters <= last code of the slice, every code of the slice has rank
+// (#splitters < code) in [b_lo, b_hi].  Codes outside [lo, hi] are clamped into the first or last
+// slice, whose bounds still hold for them.  The 32-bit entry holds b_lo (bits 0-15), a flag for
+// one candidate (bit 30: b_hi == b_lo + 1) and a flag for several (bit 31: b_hi > b_lo + 1).
+// The one candidate s0 = spl[b_lo] settles both the rank (b_lo + [s0 < code]) and the equality
+// test (code == s0), as splitter b_lo + 1, if any, lies above the slice and cannot equal a code
+// in it; with no candidate the rank is b_lo.  Only lanes whose slice holds a candidate read spl,
+// so most lookups cost one 4-byte shared load; slices with several candidates take the tree.
 // 4096 entries of 4 bytes (16 KB) for both key widths.
 template <class U>
 __host__ __device__ constexpr int pref_bits() { return 12; }
 template <class U>
 __host__ __device__ constexpr int pref_entries() { return 1 << pref_bits<U>(); }
 
-// One slice: its rank bounds, b_lo | b_hi << 16.
+// One slice: b_lo | one-candidate flag << 30 | several-candidates flag << 31.
 using PrefEnt = uint32_t;
+constexpr uint32_t kPrefOne = 1u << 30, kPrefMany = 1u << 31;
 // Bytes of one task's prefilter table, the same for both key widths.
 constexpr size_t kPrefTableBytes = 16384;
 static_assert(pref_entries<uint32_t>() * sizeof(PrefEnt) == kPrefTableBytes &&
@@ -259,9 +261,9 @@ __device__ __forceinline__ int classify_fast(U code, const U* __restrict__ tree,
   constexpr int B = 1 << LOGB;
   const U y = code < pf.lo ? pf.lo : (code > pf.hi ? pf.hi : code);
   const uint32_t e = tab[(uint32_t)((y - pf.lo) >> pf.shift)];
-  const int blo = (int)(e & 0xFFFFu), bhi = (int)(e >> 16);
-  if (bhi - blo <= 1) {
-    const bool cand = blo < bhi;
+  if (!(e & kPrefMany)) {
+    const int blo = (int)(e & 0xFFFFu);
+    const bool cand = (e & kPrefOne) != 0u;
     U s0 = U(0);
     if (cand) s0 = spl[blo];
     return blo + ((cand && s0 < code) ? 1 : 0) + ((cand && code == s0) ? B : 0);
@@ -298,23 +300,21 @@ struct SplitterClassifier {
     U s0[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {  // candidate splitters, read only where the slice has one
-      const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
       s0[i] = U(0);
-      if (blo < bhi) s0[i] = spl[blo];
+      if (e[i] & kPrefOne) s0[i] = spl[e[i] & 0xFFFFu];
     }
-    bool wide = false;
+    uint32_t any = 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-      const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
-      const bool cand = blo < bhi;
+      const int blo = (int)(e[i] & 0xFFFFu);
+      const bool cand = (e[i] & kPrefOne) != 0u;
       slot[i] = blo + ((cand && s0[i] < code[i]) ? 1 : 0) + ((cand && code[i] == s0[i]) ? B : 0);
-      wide |= bhi - blo > 1;
+      any |= e[i];
     }
-    if (wide) {
+    if (any & kPrefMany) {
 #pragma unroll
       for (int i = 0; i < N; ++i) {
-        const int blo = (int)(e[i] & 0xFFFFu), bhi = (int)(e[i] >> 16);
-        if (bhi - blo > 1) {
+        if (e[i] & kPrefMany) {
           int j = 1;
 #pragma unroll
           for (int l = 0; l < LOGB; ++l) j = 2 * j + (code[i] > tree[j] ? 1 : 0);
@@ -439,7 +439,7 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
       const int m = (a2 + c2) >> 1;
       if (s[(m + 1) * step - 1] <= last) a2 = m + 1; else c2 = m;
     }
-    tab[k] = (uint32_t)a | ((uint32_t)a2 << 16);
+    tab[k] = (uint32_t)a | (a2 == a + 1 ? kPrefOne : 0u) | (a2 > a + 1 ? kPrefMany : 0u);
   }
 }
 
@@ -1261,6 +1261,7 @@ constexpr size_t base_sort_smem() {
 // sizes are skewed (one duplicated value can hold most of the array), so the work is cut into
 // tiles of TILE elements over all items: copy_plan_kernel numbers the tiles (one CTA; tile0[k] =
 // first tile of item k, tile0[n] = total), and every CTA of copy_kernel takes tiles grid-strided.
+// When every item fits one tile (tile0 == nullptr) tile k is item k and no numbering is needed.
 template <int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS)
 copy_plan_kernel(const Item* __restrict__ items, int n, uint32_t* __restrict__ tile0) {
@@ -1304,15 +1305,15 @@ copy_kernel(const Item* __restrict__ items, int n, const uint32_t* __restrict__ 
             typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
             const typename Key<KT>::U* __restrict__ tmpk, const typename Val<VB>::T* __restrict__ tmpv) {
   static_assert(TILE % THREADS == 0, "tile shape");
-  const uint32_t total = tile0[n];
+  const uint32_t total = tile0 ? tile0[n] : (uint32_t)n;  // no numbering: one tile per item
   for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
-    int a = 0, b = n - 1;  // the item holding tile t: last k with tile0[k] <= t
+    int a = tile0 ? 0 : (int)t, b = tile0 ? n - 1 : (int)t;  // the item holding tile t: last k with tile0[k] <= t
     while (a < b) {
       const int m = (a + b + 1) >> 1;
       if (tile0[m] <= t) a = m; else b = m - 1;
     }
     const Item it = items[a];
-    const int64_t e0 = (int64_t)(t - tile0[a]) * TILE;
+    const int64_t e0 = tile0 ? (int64_t)(t - tile0[a]) * TILE : 0;
     const int64_t len = (int64_t)it.size - e0 < TILE ? (int64_t)it.size - e0 : TILE;
     const int64_t base = it.begin + e0;
 #pragma unroll 8

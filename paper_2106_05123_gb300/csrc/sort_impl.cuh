@@ -102,7 +102,7 @@ struct Shape {
   static constexpr int kCountTile = 16384 / KS;
   static constexpr int kCountStages = 3;
   static constexpr size_t kCountSmem = (size_t)kCountStages * kCountTile * KS;
-  static constexpr int kSampleThreads = 512;
+  static constexpr int kSampleThreads = 1024;
   // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
   // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits)
   static constexpr int kBaseItems = (KS == 4 && VB == 0) ? 32 : (KS == 4 ? 16 : 8);
@@ -731,14 +731,18 @@ class PlainSorter {
       base_elems = 0;
     }
     if (h.n_copy) {
-      // the tile numbering lives in the counts region, free between a level's scatter and the
-      // next level's count (item_cap + 1 words always fit: it holds at least 4096 bytes per task)
+      // The tile numbering lives in the counts region, free between a level's scatter and the
+      // next level's count (item_cap + 1 words always fit: it holds at least 4096 bytes per task).
+      // With at most one tile's elements in total every item fits one tile: no numbering.
       LaunchScope ls("copy", st_, 2.0 * (double)h.copy_elems * (KS + VB));
-      uint32_t* tile0 = counts_;
-      copy_plan_kernel<1024, kCopyTile><<<1, 1024, 0, st_>>>(copy_items_, (int)h.n_copy, tile0);
-      copy_kernel<KT, VB, 256, kCopyTile><<<(unsigned)(a_.num_sms * 8), 256, 0, st_>>>(
+      uint32_t* tile0 = h.copy_elems > (unsigned long long)kCopyTile ? counts_ : nullptr;
+      if (tile0) {
+        copy_plan_kernel<1024, kCopyTile><<<1, 1024, 0, st_>>>(copy_items_, (int)h.n_copy, tile0);
+        note_launch_count(1);
+      }
+      const int64_t blocks = std::min<int64_t>(a_.num_sms * 8, tile0 ? INT32_MAX : (int64_t)h.n_copy);
+      copy_kernel<KT, VB, 256, kCopyTile><<<(unsigned)blocks, 256, 0, st_>>>(
           copy_items_, (int)h.n_copy, tile0, keys_, vals_, tmpk_, tmpv_);
-      note_launch_count(1);
     }
     PDQ_LAUNCHED("copy");
     if (h.n_fallback) {
