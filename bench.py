@@ -151,15 +151,40 @@ def measured_peak_gbs() -> tuple[float, str]:
 
 
 # Sources that define the plain path's kernels and their launch shapes (device code, tile and
-# chunk sizes, workspace layout); a DRAM-traffic figure is valid only for these exact files.
+# chunk sizes, workspace layout); a DRAM-traffic figure is valid only for this exact code.
 KERNEL_SOURCES = ("common.cuh", "tile_pipe.cuh", "kernels.cuh", "sort_impl.cuh", "sort_api.h", "learned.cuh")
+
+
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments, whitespace runs collapsed (string and character
+    literals kept as written), so that a comment-only edit leaves the code hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_05123_gb300", "csrc")
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(strip_comments(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -18,6 +18,8 @@
 //                       more than 7/8 of its parent is a bad split and decrements the subtree's
 //                       counter; at 0 the bin goes to the fallback (Sec. 4.1)
 //   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1)
+//   copy_plan_kernel, copy_kernel - final buckets left in the temp buffer go home, decoded, in
+//                       tiles spread over all such buckets
 //   merge_tile_kernel - tiled merge-path merge (the O(n log n) fallback's passes, Sec. 4.1, and
 //                       the nearly-sorted fix-up's final merge); merge_pass_kernel serves
 //                       passes whose run pairs are shorter than a tile
