@@ -124,12 +124,6 @@ __host__ __device__ __forceinline__ int ilog2_floor(uint64_t x) {
   return r;
 }
 
-__host__ __device__ __forceinline__ uint32_t next_pow2_u32(uint32_t x) {
-  uint32_t p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
 // ------------------------------------------------------------------ host-side launch bookkeeping
 void note_launch(const char* name, cudaStream_t s, double bytes);    // before a launch
 void note_launch_end(const char* name, cudaStream_t s);              // after a launch

@@ -1,11 +1,8 @@
 // Tile staging for the streaming kernels: 1-D bulk copies (TMA engine, cp.async.bulk) from
-// global into shared memory, completion tracked by mbarriers.
-//
-// A tile [s, e) of elements of size ES lives in a shared buffer whose element k holds global
-// element s_al + k, s_al = s rounded down to a 16-byte boundary.  The 16-byte-aligned interior
-// [as, ae) is one bulk copy; the ragged head [s, as) and tail [ae, e) (fewer than 16/ES elements
-// each) are fetched with plain loads by a few threads and stored into the buffer before the
-// consuming barrier.  Every wait is bounded: after kWaitNs of polling the waiter reports failure.
+// global into shared memory with completion tracked by mbarriers, and per-thread cp.async
+// copies.  A bulk copy moves a 16-byte-aligned interior; the kernels fetch a window's ragged
+// ends (fewer than 16 bytes) with plain loads.  Every mbarrier wait is bounded: after kWaitNs
+// of polling the waiter reports failure.
 #pragma once
 
 #include "common.cuh"
@@ -67,30 +64,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (global_ns() - t0 > kWaitNs) return false;
   return true;
 }
-
-// Geometry of one tile of elements of ES bytes inside its 16-byte-aligned shared buffer.
-template <int ES>
-struct TileGeom {
-  static constexpr int kAlign = 16 / ES;  // elements per 16 bytes
-  int64_t s_al;   // global index held by buffer element 0
-  int64_t as, ae; // bulk-copied interior [as, ae)
-  int head, tail; // ragged elements [s, as) and [ae, e)
-  int off;        // buffer index of the tile's first element (s - s_al)
-
-  __device__ __forceinline__ TileGeom(int64_t s, int64_t e) {
-    s_al = s - (s % kAlign);
-    int64_t a = s_al == s ? s : s_al + kAlign;
-    as = a < e ? a : e;
-    int64_t b = e - (e % kAlign);
-    ae = b > as ? b : as;
-    head = (int)(as - s);
-    tail = (int)(e - ae);
-    off = (int)(s - s_al);
-  }
-  __device__ __forceinline__ uint32_t bulk_bytes() const { return (uint32_t)((ae - as) * ES); }
-  // global index of ragged element j (j < head + tail)
-  __device__ __forceinline__ int64_t edge(int64_t s, int j) const { return j < head ? s + j : ae + (j - head); }
-};
 
 // Asynchronous global -> shared copies of N = 4, 8 or 16 bytes per thread (cp.async, no register
 // staging); commit closes this thread's group, wait<K> blocks until at most K of its groups are
