@@ -49,7 +49,21 @@
 extern "C" {
 #endif
 
-typedef enum { PDQ_I32 = 0, PDQ_U32 = 1, PDQ_I64 = 2, PDQ_U64 = 3, PDQ_F32 = 4 } pdq_dtype;
+/* Key types.  The two composite types are 8-byte records of two 4-byte fields, field 0 at the
+ * lower address (offset 0) and field 1 at offset 4, ordered lexicographically: by field 0, then
+ * by field 1 (the "small tuples" a branchless comparison sort handles, Sec. 5.3):
+ *   PDQ_I32I32: field 0 int32, field 1 int32 (both numeric order);
+ *   PDQ_F32U32: field 0 float32 in IEEE 754 totalOrder, field 1 uint32 (e.g. a score and an id).
+ * Their key pointer needs 8-byte alignment, like int64 keys. */
+typedef enum {
+  PDQ_I32 = 0,
+  PDQ_U32 = 1,
+  PDQ_I64 = 2,
+  PDQ_U64 = 3,
+  PDQ_F32 = 4,
+  PDQ_I32I32 = 5,
+  PDQ_F32U32 = 6
+} pdq_dtype;
 
 typedef enum {
   PDQ_OK = 0,

@@ -7,7 +7,8 @@ it never imports the GPU library.
 Contents (all compiled from the C++ sources beside this file into ``liboracle.so``):
 
 * ``pdqsort(a)``: the paper's sort, in place, on a numpy array of int32/uint32/int64/uint64/
-  float32 (float32 under IEEE 754 totalOrder).  Returns the instrumentation counters
+  float32 (float32 under IEEE 754 totalOrder) or of the composite records TUPLE_I32I32 /
+  TUPLE_F32U32 (two 4-byte fields, lexicographic).  Returns the instrumentation counters
   (comparisons, heapsort fallbacks, bad partitions, ...).
 * ``pdqsort_pairs(keys, vals)``: the same on key/value records (values ride with their key).
 * ``pdqsort_segmented(a, offsets)``: each segment sorted independently.
@@ -81,12 +82,18 @@ def lib() -> ctypes.CDLL:
         return _lib
 
 
+# composite keys: records of two 4-byte fields, ordered lexicographically (first, then second)
+TUPLE_I32I32 = np.dtype([("first", "<i4"), ("second", "<i4")])
+TUPLE_F32U32 = np.dtype([("first", "<f4"), ("second", "<u4")])
+
 _DT = {
     np.dtype(np.int32): "i32",
     np.dtype(np.uint32): "u32",
     np.dtype(np.int64): "i64",
     np.dtype(np.uint64): "u64",
     np.dtype(np.float32): "f32",
+    TUPLE_I32I32: "i32i32",
+    TUPLE_F32U32: "f32u32",
 }
 
 

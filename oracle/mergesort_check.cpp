@@ -7,7 +7,8 @@
 //     plain comparisons of the native type;
 //   * float32: IEEE 754-2008 totalOrder expressed as a signed 64-bit rank: a positive-signed
 //     datum ranks by its 31 magnitude bits (0 .. 2^31-1), a negative-signed one by
-//     -(magnitude bits) - 1, so -0 ranks -1 < +0 at 0, -NaN lowest, +NaN highest.
+//     -(magnitude bits) - 1, so -0 ranks -1 < +0 at 0, -NaN lowest, +NaN highest;
+//   * composite records: the pair (rank of field 0, rank of field 1), compared first by field 0.
 // The sort is stable, so for pairs it yields one particular valid order (ties by input order).
 
 #include <cstdint>
@@ -27,6 +28,26 @@ template <class K>
 inline bool key_before(const K& a, const K& b) { return a < b; }
 template <>
 inline bool key_before<float>(const float& a, const float& b) { return float_rank(a) < float_rank(b); }
+
+// Composite records (two 4-byte fields), ordered by the pair of exact ranks (first, second).
+struct RecI32I32 {
+  int32_t first, second;
+};
+struct RecF32U32 {
+  float first;
+  uint32_t second;
+};
+template <>
+inline bool key_before<RecI32I32>(const RecI32I32& a, const RecI32I32& b) {
+  const int64_t a1 = a.first, b1 = b.first, a2 = a.second, b2 = b.second;
+  return a1 != b1 ? a1 < b1 : a2 < b2;
+}
+template <>
+inline bool key_before<RecF32U32>(const RecF32U32& a, const RecF32U32& b) {
+  const int64_t a1 = float_rank(a.first), b1 = float_rank(b.first);
+  const int64_t a2 = a.second, b2 = b.second;
+  return a1 != b1 ? a1 < b1 : a2 < b2;
+}
 
 template <class K, class V>
 void merge_rec(K* k, V* v, K* tk, V* tv, int64_t lo, int64_t hi, bool with_vals) {
@@ -72,4 +93,6 @@ void check_mergesort_u32(uint32_t* k, uint32_t* v, int64_t n) { msort<uint32_t, 
 void check_mergesort_i64(int64_t* k, uint32_t* v, int64_t n) { msort<int64_t, uint32_t>(k, v, n); }
 void check_mergesort_u64(uint64_t* k, uint32_t* v, int64_t n) { msort<uint64_t, uint32_t>(k, v, n); }
 void check_mergesort_f32(float* k, uint32_t* v, int64_t n) { msort<float, uint32_t>(k, v, n); }
+void check_mergesort_i32i32(RecI32I32* k, uint32_t* v, int64_t n) { msort<RecI32I32, uint32_t>(k, v, n); }
+void check_mergesort_f32u32(RecF32U32* k, uint32_t* v, int64_t n) { msort<RecF32U32, uint32_t>(k, v, n); }
 }

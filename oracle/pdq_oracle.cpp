@@ -30,7 +30,8 @@
 // Block partitioning (Sec. 5.3) changes speed, not results, and is not part of the oracle.
 //
 // Float32 keys are ordered by IEEE 754-2008 totalOrder (Sec. 5.10 of that standard), with the
-// order among NaNs of one sign fixed by their payload bits.
+// order among NaNs of one sign fixed by their payload bits.  Composite keys (two 4-byte fields)
+// are ordered lexicographically by their fields' orders.
 
 #include <cstdint>
 #include <cstring>
@@ -84,6 +85,31 @@ struct TotalOrderLess {
     return neg_a ? (mag_a > mag_b) : (mag_a < mag_b);
   }
 };
+
+// Composite keys (the "small tuples" of Sec. 5.3): records of two 4-byte fields compared
+// lexicographically, which is a strict weak order whenever each field's order is one: the first
+// field decides unless the two first fields are equivalent (neither below the other), then the
+// second field decides.
+struct TupleI32I32 {
+  int32_t first;
+  int32_t second;
+};
+struct TupleF32U32 {
+  float first;      // IEEE 754 totalOrder
+  uint32_t second;  // numeric order
+};
+template <class T, class FirstLess, class SecondLess>
+struct LexLess {
+  bool operator()(const T& a, const T& b) const {
+    const FirstLess f;
+    if (f(a.first, b.first)) return true;
+    if (f(b.first, a.first)) return false;
+    return SecondLess{}(a.second, b.second);
+  }
+};
+using LexLessI32I32 = LexLess<TupleI32I32, NumericLess<int32_t>, NumericLess<int32_t>>;
+using LexLessF32U32 = LexLess<TupleF32U32, TotalOrderLess, NumericLess<uint32_t>>;
+static_assert(sizeof(TupleI32I32) == 8 && sizeof(TupleF32U32) == 8, "8-byte records");
 
 // A key/value record; ordering looks at the key only (values ride along).
 template <class K, class V>
@@ -392,6 +418,12 @@ void oracle_pdqsort_u64(uint64_t* a, int64_t n, const oracle_params* p, oracle_s
 void oracle_pdqsort_f32(float* a, int64_t n, const oracle_params* p, oracle_stats* st) {
   run(a, n, TotalOrderLess{}, p, st);
 }
+void oracle_pdqsort_i32i32(TupleI32I32* a, int64_t n, const oracle_params* p, oracle_stats* st) {
+  run(a, n, LexLessI32I32{}, p, st);
+}
+void oracle_pdqsort_f32u32(TupleF32U32* a, int64_t n, const oracle_params* p, oracle_stats* st) {
+  run(a, n, LexLessF32U32{}, p, st);
+}
 
 #define ORACLE_PAIRS(NAME, K, LESS)                                                           \
   void oracle_pdqsort_pairs_##NAME##_v32(K* k, uint32_t* v, int64_t n, const oracle_params* p, \
@@ -407,6 +439,8 @@ ORACLE_PAIRS(u32, uint32_t, NumericLess<uint32_t>)
 ORACLE_PAIRS(i64, int64_t, NumericLess<int64_t>)
 ORACLE_PAIRS(u64, uint64_t, NumericLess<uint64_t>)
 ORACLE_PAIRS(f32, float, TotalOrderLess)
+ORACLE_PAIRS(i32i32, TupleI32I32, LexLessI32I32)
+ORACLE_PAIRS(f32u32, TupleF32U32, LexLessF32U32)
 #undef ORACLE_PAIRS
 
 // Sort int64 items with a caller-supplied strict-weak-order callback (returns nonzero for
@@ -428,6 +462,8 @@ ORACLE_SEG(u32, uint32_t, NumericLess<uint32_t>)
 ORACLE_SEG(i64, int64_t, NumericLess<int64_t>)
 ORACLE_SEG(u64, uint64_t, NumericLess<uint64_t>)
 ORACLE_SEG(f32, float, TotalOrderLess)
+ORACLE_SEG(i32i32, TupleI32I32, LexLessI32I32)
+ORACLE_SEG(f32u32, TupleF32U32, LexLessF32U32)
 #undef ORACLE_SEG
 
 }  // extern "C"

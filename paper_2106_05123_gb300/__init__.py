@@ -21,6 +21,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpdq.so")
 
 PDQ_I32, PDQ_U32, PDQ_I64, PDQ_U64, PDQ_F32 = 0, 1, 2, 3, 4
+# composite keys: 8-byte records {field 0, field 1}, ordered by field 0, then field 1
+PDQ_I32I32, PDQ_F32U32 = 5, 6
+KEY_BYTES = {PDQ_I32: 4, PDQ_U32: 4, PDQ_F32: 4, PDQ_I64: 8, PDQ_U64: 8, PDQ_I32I32: 8, PDQ_F32U32: 8}
 _STATUS = {0: "PDQ_OK", -1: "PDQ_ERR_ARG", -2: "PDQ_ERR_DTYPE", -3: "PDQ_ERR_WORKSPACE",
            -4: "PDQ_ERR_CUDA", -5: "PDQ_ERR_TIMEOUT", -6: "PDQ_ERR_INTERNAL"}
 
@@ -166,12 +169,35 @@ def _require_cuda(t: torch.Tensor, what: str) -> None:
         raise PdqError(-1, f"{what} must be contiguous")
 
 
+def _key_code(keys: torch.Tensor, key_dtype: int | None) -> int:
+    """The PDQ_* code of the keys: the tensor's own dtype, or the override, whose key width must
+    match the tensor's element size (composite keys are passed as an 8-byte view)."""
+    if key_dtype is None:
+        return key_dtype_code(keys.dtype)
+    code = int(key_dtype)
+    if code in KEY_BYTES and KEY_BYTES[code] != keys.element_size():
+        raise PdqError(-1, f"key_dtype {code} needs {KEY_BYTES[code]}-byte elements, "
+                           f"the tensor has {keys.element_size()}-byte elements")
+    return code
+
+
+def composite_keys(fields: torch.Tensor) -> torch.Tensor:
+    """View an (n, 2) contiguous tensor of 4-byte fields (int32 for PDQ_I32I32; float32 field 0
+    and uint32 bits of field 1 for PDQ_F32U32, e.g. an int32 or float32 tensor holding both) as
+    the 1-D tensor of n 8-byte records that the composite key types sort."""
+    if fields.dim() != 2 or fields.shape[1] != 2 or fields.element_size() != 4:
+        raise PdqError(-1, "composite keys are an (n, 2) tensor of 4-byte fields")
+    if not fields.is_contiguous():
+        raise PdqError(-1, "composite keys must be contiguous")
+    return fields.view(torch.int64).view(-1)
+
+
 def pdq_sort_keys(keys: torch.Tensor, workspace: torch.Tensor | None = None, tuning=None,
                   stream=None, key_dtype: int | None = None) -> dict:
     """Sort a 1-D CUDA tensor in place (ascending; float32 in IEEE totalOrder).  ``key_dtype``
     (a PDQ_* code) overrides the tensor's dtype, e.g. to sort an int32 view as uint32."""
     _require_cuda(keys, "keys")
-    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    dt = _key_code(keys, key_dtype)
     n = keys.numel()
     ws = workspace if workspace is not None else workspace_for(n, dt, 0, 0, keys.device)
     st = Stats()
@@ -188,7 +214,7 @@ def pdq_sort_pairs(keys: torch.Tensor, vals: torch.Tensor, workspace: torch.Tens
     if vals.numel() != keys.numel():
         raise PdqError(-1, "keys and vals differ in length")
     vb = vals.element_size()
-    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    dt = _key_code(keys, key_dtype)
     n = keys.numel()
     ws = workspace if workspace is not None else workspace_for(n, dt, vb, 0, keys.device)
     st = Stats()
@@ -210,7 +236,7 @@ def pdq_sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, vals: torch.Te
         _require_cuda(vals, "vals")
         if vals.numel() != keys.numel():
             raise PdqError(-1, "keys and vals differ in length")
-    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    dt = _key_code(keys, key_dtype)
     vb = vals.element_size() if vals is not None else 0
     n = keys.numel()
     nseg = max(0, offsets.numel() - 1)
@@ -232,7 +258,7 @@ def pdq_autotune(keys: torch.Tensor, vals: torch.Tensor | None = None, offsets: 
     ``offsets`` when given) and record the fastest for this call shape; later sorts of the same
     shape class that pass no tuning use it.  Returns (tuning, milliseconds)."""
     _require_cuda(keys, "keys")
-    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    dt = _key_code(keys, key_dtype)
     vb = vals.element_size() if vals is not None else 0
     n = keys.numel()
     nseg = max(0, offsets.numel() - 1) if offsets is not None else 0
@@ -330,7 +356,7 @@ def pdq_sort_keys_noalloc(keys: torch.Tensor, stream=None, key_dtype: int | None
     """Keys-only sort that allocates nothing: its scratch is the library's fixed 64 MiB device
     array (n <= 2^20).  For callers that cannot allocate device memory."""
     _require_cuda(keys, "keys")
-    dt = key_dtype_code(keys.dtype) if key_dtype is None else int(key_dtype)
+    dt = _key_code(keys, key_dtype)
     st = Stats()
     _check(lib().pdq_sort_keys_noalloc(keys.data_ptr(), keys.numel(), dt, _stream_ptr(stream),
                                        ctypes.byref(st)))

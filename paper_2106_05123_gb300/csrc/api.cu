@@ -95,7 +95,7 @@ static void resolve_pending() {
 static int key_bytes(int dt) {
   switch (dt) {
     case PDQ_I32: case PDQ_U32: case PDQ_F32: return 4;
-    case PDQ_I64: case PDQ_U64: return 8;
+    case PDQ_I64: case PDQ_U64: case PDQ_I32I32: case PDQ_F32U32: return 8;
     default: return 0;
   }
 }
@@ -161,6 +161,8 @@ static int dispatch_sort(int dt, const SortArgs& a, pdq_stats* st) {
     case PDQ_I64: return sort_impl<PDQ_I64, VB>(a, st);
     case PDQ_U64: return sort_impl<PDQ_U64, VB>(a, st);
     case PDQ_F32: return sort_impl<PDQ_F32, VB>(a, st);
+    case PDQ_I32I32: return sort_impl<PDQ_I32I32, VB>(a, st);
+    case PDQ_F32U32: return sort_impl<PDQ_F32U32, VB>(a, st);
     default: return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
   }
 }
@@ -173,6 +175,8 @@ static int dispatch_seg(int dt, const SegArgs& a, pdq_stats* st) {
     case PDQ_I64: return seg_sort_impl<PDQ_I64, VB>(a, st);
     case PDQ_U64: return seg_sort_impl<PDQ_U64, VB>(a, st);
     case PDQ_F32: return seg_sort_impl<PDQ_F32, VB>(a, st);
+    case PDQ_I32I32: return seg_sort_impl<PDQ_I32I32, VB>(a, st);
+    case PDQ_F32U32: return seg_sort_impl<PDQ_F32U32, VB>(a, st);
     default: return set_error(PDQ_ERR_DTYPE, "unknown key dtype");
   }
 }
@@ -185,6 +189,8 @@ static size_t dispatch_seg_ws(int dt, int64_t n, int64_t nseg) {
     case PDQ_I64: return seg_workspace_bytes_impl<PDQ_I64, VB>(n, nseg);
     case PDQ_U64: return seg_workspace_bytes_impl<PDQ_U64, VB>(n, nseg);
     case PDQ_F32: return seg_workspace_bytes_impl<PDQ_F32, VB>(n, nseg);
+    case PDQ_I32I32: return seg_workspace_bytes_impl<PDQ_I32I32, VB>(n, nseg);
+    case PDQ_F32U32: return seg_workspace_bytes_impl<PDQ_F32U32, VB>(n, nseg);
     default: return 0;
   }
 }
@@ -197,6 +203,8 @@ static size_t dispatch_ws(int dt, int64_t n) {
     case PDQ_I64: return workspace_bytes_impl<PDQ_I64, VB>(n);
     case PDQ_U64: return workspace_bytes_impl<PDQ_U64, VB>(n);
     case PDQ_F32: return workspace_bytes_impl<PDQ_F32, VB>(n);
+    case PDQ_I32I32: return workspace_bytes_impl<PDQ_I32I32, VB>(n);
+    case PDQ_F32U32: return workspace_bytes_impl<PDQ_F32U32, VB>(n);
     default: return 0;
   }
 }

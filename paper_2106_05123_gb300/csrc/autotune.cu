@@ -45,7 +45,7 @@ ShapeKey shape_of(bool seg, int dt, int vb, int64_t n, int64_t nseg) {
 int key_bytes_of(int dt) {
   switch (dt) {
     case PDQ_I32: case PDQ_U32: case PDQ_F32: return 4;
-    case PDQ_I64: case PDQ_U64: return 8;
+    case PDQ_I64: case PDQ_U64: case PDQ_I32I32: case PDQ_F32U32: return 8;
     default: return 0;
   }
 }

@@ -105,6 +105,27 @@ template <> struct Key<PDQ_I64> {
   static __host__ __device__ __forceinline__ U enc(U x) { return x ^ 0x8000000000000000ull; }
   static __host__ __device__ __forceinline__ U dec(U x) { return x ^ 0x8000000000000000ull; }
 };
+// Composite keys: an 8-byte record {field 0, field 1} read as one little-endian word (field 0 in
+// the low half).  The code puts field 0's code in the high half and field 1's in the low half, so
+// the unsigned order of codes is the lexicographic order of the records.
+template <> struct Key<PDQ_I32I32> {
+  using U = uint64_t;
+  static __host__ __device__ __forceinline__ U enc(U x) {
+    return ((U)(Key<PDQ_I32>::enc((uint32_t)x)) << 32) | Key<PDQ_I32>::enc((uint32_t)(x >> 32));
+  }
+  static __host__ __device__ __forceinline__ U dec(U c) {
+    return (U)Key<PDQ_I32>::dec((uint32_t)(c >> 32)) | ((U)Key<PDQ_I32>::dec((uint32_t)c) << 32);
+  }
+};
+template <> struct Key<PDQ_F32U32> {
+  using U = uint64_t;
+  static __host__ __device__ __forceinline__ U enc(U x) {
+    return ((U)(Key<PDQ_F32>::enc((uint32_t)x)) << 32) | (x >> 32);
+  }
+  static __host__ __device__ __forceinline__ U dec(U c) {
+    return (U)Key<PDQ_F32>::dec((uint32_t)(c >> 32)) | ((c & 0xFFFFFFFFull) << 32);
+  }
+};
 
 // Value payload: VB = 0 (none), 4 or 8 bytes.
 template <int VB> struct Val { using T = uint32_t; };

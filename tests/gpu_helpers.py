@@ -4,6 +4,7 @@ import numpy as np
 import torch
 
 import paper_2106_05123_gb300 as pdq
+import workloads
 
 CODE = {
     np.dtype(np.int32): pdq.PDQ_I32,
@@ -11,6 +12,8 @@ CODE = {
     np.dtype(np.int64): pdq.PDQ_I64,
     np.dtype(np.uint64): pdq.PDQ_U64,
     np.dtype(np.float32): pdq.PDQ_F32,
+    workloads.COMPOSITE_DTYPES["i32i32"]: pdq.PDQ_I32I32,
+    workloads.COMPOSITE_DTYPES["f32u32"]: pdq.PDQ_F32U32,
 }
 # transport dtypes: unsigned keys travel as same-width signed tensors (the ABI takes raw bits)
 CARRIER = {4: (np.int32, torch.int32), 8: (np.int64, torch.int64)}

@@ -48,6 +48,12 @@ def test_workspace_bytes_is_host_logic(L):
     assert seg >= big                     # the segmented layout also covers the plain one
     assert big >= 4 * (1 << 20)          # at least the temp key buffer
     assert pdq.pdq_workspace_bytes(10, 7, 0) == 0       # unknown dtype
+    # composite keys (two 4-byte fields) take the 8-byte layout
+    for code in (pdq.PDQ_I32I32, pdq.PDQ_F32U32):
+        for vb in (0, 4, 8):
+            assert pdq.pdq_workspace_bytes(1 << 20, code, vb) == pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_U64, vb)
+        assert (pdq.pdq_workspace_bytes(1 << 20, code, 0, num_segments=300)
+                == pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_U64, 0, num_segments=300))
     assert pdq.pdq_workspace_bytes(10, pdq.PDQ_I32, 3) == 0
 
 

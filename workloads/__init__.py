@@ -176,6 +176,33 @@ def normal_f32_specials(n: int, seed: int, frac: float = 0.001):
 
 
 # ------------------------------------------------------------------ segmented configuration
+# composite keys: records of two 4-byte fields (field 0 at the lower address)
+COMPOSITE_DTYPES = {
+    "i32i32": np.dtype([("first", "<i4"), ("second", "<i4")]),
+    "f32u32": np.dtype([("first", "<f4"), ("second", "<u4")]),
+}
+
+
+def composite_keys(kind: str, n: int, seed: int, first_distinct: int = 0) -> np.ndarray:
+    """n records of the composite key type `kind` ("i32i32" or "f32u32").  Field 0: uniform bits
+    (i32i32) or N(0,1) float32 with 1% NaN / -0.0 / +-inf (f32u32); with first_distinct > 0 it is
+    drawn from that many distinct values, so long runs of equal first fields are decided by field
+    1.  Field 1: uniform bits."""
+    dt = COMPOSITE_DTYPES[kind]
+    out = np.empty(n, dtype=dt)
+    if kind == "i32i32":
+        first = uniform_bits(n, np.int32, substream(seed, 21))
+    else:
+        first, _ = normal_f32_specials(n, substream(seed, 22), frac=0.01)
+    if first_distinct > 0 and n:
+        pool = first[: min(n, first_distinct)].copy()
+        pick = (splitmix64(substream(seed, 23), n) % np.uint64(pool.size)).astype(np.int64)
+        first = pool[pick]
+    out["first"] = first
+    out["second"] = uniform_bits(n, dt["second"], substream(seed, 24))
+    return out
+
+
 def segment_offsets(num_segments: int, seed: int, max_log2: int = 16) -> np.ndarray:
     """Offsets (int64, num_segments + 1) for lengths clamp(round(2^(max_log2 * U)), 1, 2^max_log2)."""
     u = uniform01(substream(seed, 7), num_segments)
