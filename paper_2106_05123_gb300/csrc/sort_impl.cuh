@@ -104,8 +104,9 @@ struct Shape {
   static constexpr size_t kCountSmem = (size_t)kCountStages * kCountTile * KS;
   static constexpr int kSampleThreads = 1024;
   // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
-  // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits)
-  static constexpr int kBaseItems = VB == 0 ? (KS == 4 ? 32 : 16) : (KS == 4 ? 16 : 8);
+  // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits); ITEMS =
+  // 32 keys per thread for 4-byte keys alone, 16 otherwise (54-79 registers, no spills)
+  static constexpr int kBaseItems = VB == 0 ? (KS == 4 ? 32 : 16) : 16;
   static constexpr int base_threads(int cls) { return (1024 << cls) / kBaseItems; }
   static constexpr int kMaxClass = (KS == 4 && VB <= 4) ? 4 : 3;
   static constexpr int kMaxCap = 1024 << kMaxClass;
