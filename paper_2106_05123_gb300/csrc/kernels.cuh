@@ -1026,7 +1026,9 @@ __device__ __forceinline__ bool precedes(U a, uint32_t ia, U b, uint32_t ib) {
   return a < b;
 }
 
-template <bool WITH_IDX, int N, class U>
+// Compile-time bitonic network over N registers.  CARRY: the index array x moves with its keys;
+// CMPIDX: ties between equal codes are broken by x (otherwise equal codes are left in any order).
+template <bool CARRY, bool CMPIDX, int N, class U>
 __device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
 #pragma unroll
   for (int kk = 2; kk <= N; kk <<= 1) {
@@ -1037,8 +1039,8 @@ __device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
         const int l = i ^ j;
         if (l > i) {
           const bool up = (i & kk) == 0;  // compile-time direction
-          if (WITH_IDX) {
-            const bool gt = precedes<true>(k[l], x[l], k[i], x[i]);
+          if (CARRY) {
+            const bool gt = precedes<CMPIDX>(k[l], x[l], k[i], x[i]);
             const bool sw = gt == up;
             const U a = k[i], b = k[l];
             const uint32_t ya = x[i], yb = x[l];
@@ -1095,134 +1097,143 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
     sk[pad_idx<U>(i)] = c;
     if (W) si[pad_idx<U>(i)] = (uint32_t)i;
   }
-  // Keys only: a sentinel (all-ones code) ties with a real all-ones code, so a bucket holding
-  // one merges with bounds tests; with values the sentinel index (all ones) breaks every tie.
+  // Without a real all-ones code every real key is below the padding and the sentinels, and
+  // equal real keys may end in any order (the sort is unstable), so codes alone are compared
+  // (CMPIDX false).  A real all-ones code ties with the sentinels and the padding: keys only,
+  // such a bucket merges with bounds tests (`checked`); with values, ties are broken by the
+  // original position (CMPIDX true: padding positions are >= m, sentinel indices all ones).
   // (the block-wide OR is also the barrier after the staging writes: always executed)
   const bool any_max = __syncthreads_or(max_code) != 0;
   const bool checked = !W && any_max;
   U k[ITEMS];
   uint32_t x[ITEMS];
   const bool active = tid < na;
-  if (active) {
-#pragma unroll
-    for (int e = 0; e < ITEMS; ++e) {
-      const int p = pad_idx<U>(tid * ITEMS + e);
-      k[e] = sk[p];
-      x[e] = W ? si[p] : 0u;
-    }
-    register_sort<W>(k, x);
-  }
-  // Merge rounds.  Before round R the registers go back to shared memory with runs of R
-  // elements, each followed by one sentinel slot (all-ones code, all-ones index).  While a pair of
-  // runs (2R elements) lies inside one warp's WSPAN = 32 * ITEMS elements, each warp keeps a fixed
-  // region of WSPAN + 32 slots (its runs and their sentinels), so the round reads only what its
-  // own warp wrote and a warp barrier suffices; wider rounds use one array-wide layout (run r at
-  // slot r * (R + 1)) and block barriers.  A thread's ITEMS elements never straddle runs.
-  constexpr int WSPAN = 32 * ITEMS;
-  constexpr int WSTRIDE = WSPAN + 32;
-  constexpr int LG_WSPAN = ITEMS == 32 ? 10 : (ITEMS == 16 ? 9 : 8);
-  static_assert((1 << LG_WSPAN) == WSPAN, "ITEMS must be 8, 16 or 32");
-  auto slot_of = [&](int pos, int lgR, bool wl) {
-    if (wl) {
-      const int lp = pos & (WSPAN - 1);
-      return (pos >> LG_WSPAN) * WSTRIDE + lp + (lp >> lgR);
-    }
-    return pos + (pos >> lgR);
-  };
-  int lg = 0;
-  while ((ITEMS << lg) < P) ++lg;
-  int R = ITEMS;
-  for (int round = 0; round < lg; ++round, R <<= 1) {
-    const int lgR = __ffs(R) - 1;
-    const bool warp_local = 2 * R <= WSPAN;
-    // the first round's layout differs from the staging layout across warps: block barrier
-    if (warp_local && round > 0) __syncwarp(); else __syncthreads();
+  auto sort_runs = [&](auto CMP) {
+    constexpr bool C = decltype(CMP)::value;
     if (active) {
-      const int pos0 = tid * ITEMS;
-      const int slot0 = slot_of(pos0, lgR, warp_local);
 #pragma unroll
       for (int e = 0; e < ITEMS; ++e) {
-        const int p = pad_idx<U>(slot0 + e);
-        sk[p] = k[e];
-        if (W) si[p] = x[e];
+        const int p = pad_idx<U>(tid * ITEMS + e);
+        k[e] = sk[p];
+        x[e] = W ? si[p] : 0u;
       }
-      if (((pos0 + ITEMS) & (R - 1)) == 0 || pos0 + ITEMS == P) {  // last thread of its run
-        const int p = pad_idx<U>(slot0 + ITEMS);
-        sk[p] = ~U(0);
-        if (W) si[p] = 0xFFFFFFFFu;
-      }
+      register_sort<W, C>(k, x);
     }
-    if (warp_local) __syncwarp(); else __syncthreads();
-    if (active) {
-      const int pos = tid * ITEMS;
-      const int g = pos & ~(2 * R - 1);             // first element of the pair of runs
-      const int d = pos - g;                        // this thread's diagonal inside the pair
-      const int a0 = slot_of(g, lgR, warp_local);   // slot of run A's first element
-      const int b0 = a0 + R + 1;                    // slot of run B's first element
-      const int la = min(R, P - g);                  // run A (may be the ragged last run)
-      const int lb = max(0, min(R, P - g - R));      // run B (may be short or empty)
-      // merge-path split: the number of A elements among the first d outputs (ties take A)
-      int lo = d > lb ? d - lb : 0;
-      int hi = d < la ? d : la;
-      for (int span = R; span > 0; span >>= 1) {  // log2(R) + 1 halvings suffice
-        if (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          const int pa = pad_idx<U>(a0 + mid), pb = pad_idx<U>(b0 + d - 1 - mid);
-          if (!precedes<W>(sk[pb], W ? si[pb] : 0u, sk[pa], W ? si[pa] : 0u)) lo = mid + 1;
-          else hi = mid;
-        }
+    // Merge rounds.  Before round R the registers go back to shared memory with runs of R
+    // elements, each followed by one sentinel slot (all-ones code, all-ones index).  While a pair of
+    // runs (2R elements) lies inside one warp's WSPAN = 32 * ITEMS elements, each warp keeps a fixed
+    // region of WSPAN + 32 slots (its runs and their sentinels), so the round reads only what its
+    // own warp wrote and a warp barrier suffices; wider rounds use one array-wide layout (run r at
+    // slot r * (R + 1)) and block barriers.  A thread's ITEMS elements never straddle runs.
+    constexpr int WSPAN = 32 * ITEMS;
+    constexpr int WSTRIDE = WSPAN + 32;
+    constexpr int LG_WSPAN = ITEMS == 32 ? 10 : (ITEMS == 16 ? 9 : 8);
+    static_assert((1 << LG_WSPAN) == WSPAN, "ITEMS must be 8, 16 or 32");
+    auto slot_of = [&](int pos, int lgR, bool wl) {
+      if (wl) {
+        const int lp = pos & (WSPAN - 1);
+        return (pos >> LG_WSPAN) * WSTRIDE + lp + (lp >> lgR);
       }
-      int ia = a0 + lo, ib = b0 + (d - lo);  // slots of the next A and B elements
-      U ka = lo < la ? sk[pad_idx<U>(ia)] : ~U(0), kb = d - lo < lb ? sk[pad_idx<U>(ib)] : ~U(0);
-      uint32_t xa = 0xFFFFFFFFu, xb = 0xFFFFFFFFu;
-      if (W) {
-        if (lo < la) xa = si[pad_idx<U>(ia)];
-        if (d - lo < lb) xb = si[pad_idx<U>(ib)];
-      }
-      if (!checked) {
-        // Sentinels end both runs, so an exhausted run is never chosen while the other still
-        // holds a smaller element.  Keys only: padding codes (all ones) tie with A's sentinel and
-        // ties take A, so A's index stops at its sentinel (those outputs are all-ones padding
-        // positions either way); with values the sentinel's all-ones index breaks every tie.
-        const int ea = a0 + la;
+      return pos + (pos >> lgR);
+    };
+    int lg = 0;
+    while ((ITEMS << lg) < P) ++lg;
+    int R = ITEMS;
+    for (int round = 0; round < lg; ++round, R <<= 1) {
+      const int lgR = __ffs(R) - 1;
+      const bool warp_local = 2 * R <= WSPAN;
+      // the first round's layout differs from the staging layout across warps: block barrier
+      if (warp_local && round > 0) __syncwarp(); else __syncthreads();
+      if (active) {
+        const int pos0 = tid * ITEMS;
+        const int slot0 = slot_of(pos0, lgR, warp_local);
 #pragma unroll
         for (int e = 0; e < ITEMS; ++e) {
-          const bool take_a = !precedes<W>(kb, xb, ka, xa);
-          if (W) {
-            k[e] = take_a ? ka : kb;
-            x[e] = take_a ? xa : xb;
+          const int p = pad_idx<U>(slot0 + e);
+          sk[p] = k[e];
+          if (W) si[p] = x[e];
+        }
+        if (((pos0 + ITEMS) & (R - 1)) == 0 || pos0 + ITEMS == P) {  // last thread of its run
+          const int p = pad_idx<U>(slot0 + ITEMS);
+          sk[p] = ~U(0);
+          if (W) si[p] = 0xFFFFFFFFu;
+        }
+      }
+      if (warp_local) __syncwarp(); else __syncthreads();
+      if (active) {
+        const int pos = tid * ITEMS;
+        const int g = pos & ~(2 * R - 1);             // first element of the pair of runs
+        const int d = pos - g;                        // this thread's diagonal inside the pair
+        const int a0 = slot_of(g, lgR, warp_local);   // slot of run A's first element
+        const int b0 = a0 + R + 1;                    // slot of run B's first element
+        const int la = min(R, P - g);                  // run A (may be the ragged last run)
+        const int lb = max(0, min(R, P - g - R));      // run B (may be short or empty)
+        // merge-path split: the number of A elements among the first d outputs (ties take A)
+        int lo = d > lb ? d - lb : 0;
+        int hi = d < la ? d : la;
+        for (int span = R; span > 0; span >>= 1) {  // log2(R) + 1 halvings suffice
+          if (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const int pa = pad_idx<U>(a0 + mid), pb = pad_idx<U>(b0 + d - 1 - mid);
+            if (!precedes<C>(sk[pb], C ? si[pb] : 0u, sk[pa], C ? si[pa] : 0u)) lo = mid + 1;
+            else hi = mid;
+          }
+        }
+        int ia = a0 + lo, ib = b0 + (d - lo);  // slots of the next A and B elements
+        U ka = lo < la ? sk[pad_idx<U>(ia)] : ~U(0), kb = d - lo < lb ? sk[pad_idx<U>(ib)] : ~U(0);
+        uint32_t xa = 0xFFFFFFFFu, xb = 0xFFFFFFFFu;
+        if (W) {
+          if (lo < la) xa = si[pad_idx<U>(ia)];
+          if (d - lo < lb) xb = si[pad_idx<U>(ib)];
+        }
+        if (!checked) {
+          // Sentinels end both runs, so an exhausted run is never chosen while the other still
+          // holds a smaller element.  Comparing codes only, padding codes (all ones) tie with A's
+          // sentinel and ties take A, so A's index stops at its sentinel (those outputs land on
+          // positions >= m, which are padding either way); with positions compared, the
+          // sentinel's all-ones index breaks every tie.
+          const int ea = a0 + la;
+#pragma unroll
+          for (int e = 0; e < ITEMS; ++e) {
+            const bool take_a = !precedes<C>(kb, xb, ka, xa);
+            if (W) {
+              k[e] = take_a ? ka : kb;
+              x[e] = take_a ? xa : xb;
+            } else {
+              k[e] = ka < kb ? ka : kb;
+            }
             ia += take_a ? 1 : 0;
-          } else {
-            k[e] = ka < kb ? ka : kb;
-            ia = min(ia + (take_a ? 1 : 0), ea);
+            if (!C) ia = min(ia, ea);
+            ib += take_a ? 0 : 1;
+            const int p = pad_idx<U>(take_a ? ia : ib);
+            const U nk = sk[p];
+            ka = take_a ? nk : ka;
+            kb = take_a ? kb : nk;
+            if (W) {
+              const uint32_t nx = si[p];
+              xa = take_a ? nx : xa;
+              xb = take_a ? xb : nx;
+            }
           }
-          ib += take_a ? 0 : 1;
-          const int p = pad_idx<U>(take_a ? ia : ib);
-          const U nk = sk[p];
-          ka = take_a ? nk : ka;
-          kb = take_a ? kb : nk;
-          if (W) {
-            const uint32_t nx = si[p];
-            xa = take_a ? nx : xa;
-            xb = take_a ? xb : nx;
-          }
-        }
-      } else {
-        // keys only with a real all-ones code: the same merge with explicit run ends
-        const int ea = a0 + la, eb = b0 + lb;
+        } else {
+          // keys only with a real all-ones code: the same merge with explicit run ends
+          const int ea = a0 + la, eb = b0 + lb;
 #pragma unroll
-        for (int e = 0; e < ITEMS; ++e) {
-          const bool take_a = ia < ea && (ib >= eb || !(kb < ka));
-          k[e] = take_a ? ka : kb;
-          ia += take_a ? 1 : 0;
-          ib += take_a ? 0 : 1;
-          const U nk = sk[pad_idx<U>(take_a ? ia : ib)];
-          ka = take_a ? nk : ka;
-          kb = take_a ? kb : nk;
+          for (int e = 0; e < ITEMS; ++e) {
+            const bool take_a = ia < ea && (ib >= eb || !(kb < ka));
+            k[e] = take_a ? ka : kb;
+            ia += take_a ? 1 : 0;
+            ib += take_a ? 0 : 1;
+            const U nk = sk[pad_idx<U>(take_a ? ia : ib)];
+            ka = take_a ? nk : ka;
+            kb = take_a ? kb : nk;
+          }
         }
       }
     }
-  }
+  };
+  if (W && any_max) sort_runs(IntC<1>());
+  else sort_runs(IntC<0>());
   __syncthreads();
   if (active) {
 #pragma unroll

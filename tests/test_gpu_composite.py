@@ -77,3 +77,25 @@ def test_composite_view_and_width_check():
     assert f.cpu().tolist() == [[-2, 5], [1, 9], [3, 0], [3, 1]]
     with pytest.raises(pdq.PdqError):
         pdq.pdq_sort_keys(torch.zeros(8, dtype=torch.int32, device="cuda"), key_dtype=pdq.PDQ_I32I32)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [1000, 4097, 100003])
+def test_composite_records_holding_the_sentinel_value(kind, n):
+    # the largest record of each order (both fields at their maximum) is the base sort's sentinel
+    a = workloads.composite_keys(kind, n, 91, first_distinct=50)
+    pos = (workloads.splitmix64(5, n // 20 + 1) % np.uint64(n)).astype(np.int64)
+    if kind == "i32i32":
+        a["first"][pos] = np.iinfo(np.int32).max
+        a["second"][pos] = np.iinfo(np.int32).max
+    else:
+        a["first"].view(np.uint32)[pos] = np.uint32(0x7FFFFFFF)
+        a["second"][pos] = np.iinfo(np.uint32).max
+    got, _, _ = gpu_sort(a)
+    assert got.tobytes() == oracle_sorted(a).tobytes()
+    vals = np.arange(n, dtype=np.uint32)
+    gk, gv, _ = gpu_sort(a, vals)
+    assert gk.tobytes() == oracle_sorted(a).tobytes()
+    idx = gv.astype(np.int64)
+    assert np.array_equal(np.sort(idx), np.arange(n))
+    assert a[idx].tobytes() == gk.tobytes()

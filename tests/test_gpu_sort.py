@@ -288,3 +288,32 @@ def test_nearly_sorted_huge_segment():
     assert rc == 0
     want = np.concatenate([np.sort(a[:big]), np.sort(a[big:])])
     assert np.array_equal(got, want)
+
+
+def with_largest_code(dtype, n, frac, seed):
+    """Keys of which about `frac` hold the largest code of their order (the base sort's sentinel
+    value: INT_MAX, UINT_MAX, or the float32 +NaN with all payload bits set)."""
+    a = keys_for(dtype, n, seed)
+    m = int(n * frac) + 1
+    pos = (workloads.splitmix64(workloads.substream(seed, 9), m) % np.uint64(max(n, 1))).astype(np.int64)
+    if dtype == np.float32:
+        a.view(np.uint32)[pos] = np.uint32(0x7FFFFFFF)
+    else:
+        a[pos] = np.iinfo(dtype).max
+    return a
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [31, 1000, 4097, 16383, 100003])
+@pytest.mark.parametrize("frac", [0.01, 0.3])
+def test_keys_holding_the_sentinel_value(dtype, n, frac):
+    # ragged sizes leave padding in the base sort, which ties with these keys
+    a = with_largest_code(dtype, n, frac, n)
+    got, _, _ = gpu_sort(a)
+    assert np.array_equal(bits(got), bits(oracle_sorted(a)))
+    vals = np.arange(n, dtype=np.uint32)
+    gk, gv, _ = gpu_sort(a, vals)
+    assert np.array_equal(bits(gk), bits(oracle_sorted(a)))
+    idx = gv.astype(np.int64)
+    assert np.array_equal(np.sort(idx), np.arange(n))
+    assert np.array_equal(bits(a[idx]), bits(gk))
