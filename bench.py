@@ -399,6 +399,22 @@ def main() -> None:
     bench_gpu(args, rank, world)
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over all ranks (every rank receives it); x itself on one rank.  `device`
+    holds the reduction tensor: cuda under NCCL, cpu under gloo."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gkeys(keys_per_rank: int, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput: every rank's keys over the slowest rank's timed milliseconds."""
+    return keys_per_rank * world / (slowest_ms * 1e-3) / 1e9
+
+
 def bench_gpu(args, rank: int, world: int) -> None:
     import torch
     import paper_2106_05123_gb300 as pdq
@@ -495,13 +511,9 @@ def bench_gpu(args, rank: int, world: int) -> None:
     launches = pdq.launch_count() - l0
     if dist is not None:
         dist.barrier()
-    total_ms = sum(a.elapsed_time(b) for a, b in events)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in events), dist, "cuda")
     keys_per_rank = n * len(pristine) * args.steps
-    value = keys_per_rank * world / (total_ms * 1e-3) / 1e9
+    value = whole_job_gkeys(keys_per_rank, world, total_ms)
 
     # dominant kernel: one more (untimed) step with the library's per-kernel event timing
     pdq.profile_reset()
