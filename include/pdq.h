@@ -14,9 +14,10 @@
  *     bucket that is final at once (Sec. 3, Lemma 4 / Theorem 1: O(nk) for k distinct keys);
  *   - sorted / reverse-sorted input exits after a probe, reversing in place when descending
  *     (Sec. 5.2);
- *   - a bucket that keeps more than 7/8 of its parent is a bad split; each subtree has a
- *     counter starting at floor(log2 n), and a bucket whose counter reaches 0 is sorted by a
- *     merge-path merge sort, the O(n log n) fallback (Sec. 4.1, Theorem 2);
+ *   - a bucket that keeps more than 7/8 of its parent's keys outside the parent's equality
+ *     buckets is a bad split; each subtree has a counter starting at floor(log2 n), and a
+ *     bucket whose counter reaches 0 is sorted by a merge-path merge sort, the O(n log n)
+ *     fallback (Sec. 4.1, Theorem 2);
  *   - fresh splitter samples after a bad split (Sec. 4.2);
  *   - small buckets are sorted in shared memory (Sec. 5.1).
  *
@@ -82,7 +83,8 @@ typedef struct {
   int64_t reversed;          /* 1 if the input was strictly non-increasing and was reversed */
   int64_t sorted_exit;       /* 1 if the probe found the input sorted (or all equal) */
   int64_t learned_overflow;  /* learned path: buckets re-partitioned by the exact repair */
-  int64_t bad_splits;        /* children that kept more than 7/8 of their parent (Sec. 4.1) */
+  int64_t bad_splits;        /* children that kept more than 7/8 of their parent's non-equal
+                                keys (Sec. 4.1) */
   int64_t base_buckets;      /* buckets finished by the shared-memory base sort (Sec. 5.1) */
   int64_t kernel_launches;   /* kernels launched by the call */
   int64_t fixup_peeled;      /* nearly-sorted fix-up: keys peeled off descents and merged back
@@ -205,11 +207,13 @@ int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dt
  * device memory is owned by a framework's allocator, fixed-budget plug-ins, latency-sensitive
  * loops where cudaMalloc/cudaFree would synchronise the device).  The paper has no counterpart:
  * this is a memory-ownership variant of pdq_sort_keys.  Its scratch is one file-scope device
- * array of 64 MiB per GPU, held until the process exits; it covers up to 2^20 keys of any key
- * type, and larger n returns PDQ_ERR_ARG with the limit in the message.  The first call on a
- * device (with that device current) looks up the array's device address; make that first call
- * before any stream capture.  All calls on a device share the array: calls that overlap on the
- * GPU race and must not be issued.  d_keys, n, key_dtype, cuda_stream, stats: as pdq_sort_keys. */
+ * array of 64 MiB per GPU, held until the process exits.  It takes at most 2^20 keys of any key
+ * type; larger n returns PDQ_ERR_ARG with the limit in the message.  Every call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress, checked); the first call
+ * on a device loads the module there, so make it before any stream capture.  All calls on a
+ * device share the array, which keeps the last call's contents (the sort re-initialises every
+ * counter and list length it reads): calls that overlap on the GPU race and must not be issued.
+ * d_keys, n, key_dtype, cuda_stream, stats: as pdq_sort_keys. */
 int pdq_sort_keys_noalloc(void* d_keys, int64_t n, pdq_dtype key_dtype, void* cuda_stream,
                           pdq_stats* stats);
 

@@ -15,8 +15,9 @@
 //                       tile in shared memory grouped by bin and writes contiguous runs
 //                       (the GPU form of block partitioning, Sec. 5.3)
 //   bookkeep_kernel   - equal bins are final; small bins go to the base sort; a bin keeping
-//                       more than 7/8 of its parent is a bad split and decrements the subtree's
-//                       counter; at 0 the bin goes to the fallback (Sec. 4.1)
+//                       more than 7/8 of its parent's non-equal keys is a bad split and
+//                       decrements the subtree's counter; at 0 the bin goes to the fallback
+//                       (Sec. 4.1)
 //   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1)
 //   copy_plan_kernel, copy_kernel - final buckets left in the temp buffer go home, decoded, in
 //                       tiles spread over all such buckets
@@ -946,6 +947,19 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   const int nb = task_nbins[task];
   const uint2 ch = b < nb ? children[(size_t)task * bin_stride + b] : make_uint2(0u, 0u);
   const Task t = tasks[task];
+  // the parent's keys outside its equality bins (every block of the task sums them itself)
+  __shared__ unsigned long long s_equal;
+  if (threadIdx.x == 0) s_equal = 0ull;
+  __syncthreads();
+  if (equal_bins) {
+    unsigned long long e = 0ull;
+    for (int j = 2 * (int)threadIdx.x + 1; j < nb; j += 2 * (int)blockDim.x)
+      e += children[(size_t)task * bin_stride + j].y;
+    e = warp_sum(e);
+    if ((threadIdx.x & 31) == 0 && e) atomicAdd(&s_equal, e);
+  }
+  __syncthreads();
+  const int64_t nonequal = t.size - (int64_t)s_equal;
   const int dst = t.buf == kBufKeys ? kBufTmp : kBufKeys;
   Item it;
   it.begin = t.begin + ch.x;
@@ -957,8 +971,9 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
   const bool equal = live && equal_bins && (b & 1);  // every key equals the splitter: final (Sec. 3)
   const bool base = live && !equal && (int64_t)ch.y <= base_cap;
   const bool split = live && !equal && !base;
-  // bad split: the child kept more than 7/8 of its parent (p = 1/8, a shift; Sec. 4.1)
-  const bool bad = split && (int64_t)ch.y > t.size - (t.size >> 3);
+  // bad split (Sec. 4.1, p = 1/8): the child kept more than floor(7/8) of the parent's keys
+  // that are not in an equality bin (those are final and are not split further)
+  const bool bad = split && (int64_t)ch.y > ((7 * nonequal) >> 3);
   const int left = t.bad_left - (bad ? 1 : 0);
   const bool fallback = split && left <= 0;
   const bool recurse = split && left > 0;

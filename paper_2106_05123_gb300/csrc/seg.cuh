@@ -8,7 +8,8 @@
 //   partition task - the CTA runs one distribution level on its own: hashed sample, splitters,
 //                    count, scan, scatter into the other buffer (Sec. 3 equal-key bins are
 //                    finished on the spot), and pushes the children; a child that keeps more
-//                    than 7/8 of its parent costs one unit of the subtree's bad-split budget,
+//                    than 7/8 of its parent's non-equal keys costs one unit of the subtree's
+//                    bad-split budget,
 //                    and at 0 it goes to the host's O(n log n) fallback (Sec. 4.1).
 // Queue slots carry ready flags; every wait is bounded in time.  If a wait gives up, the
 // kernel records a timeout and switches to salvage mode: remaining tasks only move their data
@@ -345,6 +346,18 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
     cp_async_wait<0>();
   });
   __syncthreads();
+  // the parent's keys outside its equality bins, for the bad-split rule (Sec. 4.1)
+  __shared__ unsigned long long s_equal;
+  if (tid == 0) s_equal = 0ull;
+  __syncthreads();
+  {
+    unsigned long long e = 0ull;
+    for (int b = 2 * tid + 1; b < nb; b += 2 * THREADS) e += hist[slot(b)];
+    e = warp_sum(e);
+    if ((tid & 31) == 0 && e) atomicAdd(&s_equal, e);
+  }
+  __syncthreads();
+  const int64_t nonequal = size - (int64_t)s_equal;
   // children
   for (int b = tid; b < nb; b += THREADS) {
     const uint32_t cnt = hist[slot(b)];
@@ -370,7 +383,8 @@ __device__ void seg_partition(const SegTask& t, const SegParams& prm, int cap, t
         atomicOr(&st->error, 2ull);
       continue;
     }
-    const bool bad = (int64_t)cnt > size - (size >> 3);  // kept more than 7/8 (Sec. 4.1)
+    // bad: kept more than floor(7/8) of the parent's non-equal keys (Sec. 4.1)
+    const bool bad = (int64_t)cnt > ((7 * nonequal) >> 3);
     if (bad) atomicAdd(&st->bad_splits, 1ull);
     const int left = (int)t.bad_left - (bad ? 1 : 0);
     c.kind = kSegPart;

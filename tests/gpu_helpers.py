@@ -3,6 +3,7 @@
 import numpy as np
 import torch
 
+import oracle
 import paper_2106_05123_gb300 as pdq
 import workloads
 
@@ -75,3 +76,10 @@ def gpu_sort_segmented(keys: np.ndarray, offsets: np.ndarray, vals: np.ndarray |
     kout = to_host(dk, keys.dtype)[:n]
     vout = to_host(dv, vals.dtype)[:n] if dv is not None else None
     return kout, vout, st.as_dict(), rc
+
+
+def oracle_sorted(a: np.ndarray) -> np.ndarray:
+    """The expected keys: the CPU oracle's pdqsort of a copy of `a`."""
+    b = np.ascontiguousarray(a).copy()
+    oracle.pdqsort(b)
+    return b

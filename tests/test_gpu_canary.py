@@ -9,7 +9,7 @@ import torch
 import oracle
 import paper_2106_05123_gb300 as pdq
 import workloads
-from gpu_helpers import CODE, bits
+from gpu_helpers import CODE, bits, oracle_sorted
 
 pytestmark = pytest.mark.gpu
 
@@ -86,7 +86,7 @@ def test_exits_and_fixup_stay_inside_their_buffers(name):
     torch.cuda.synchronize()
     assert rc == 0
     assert _margins_intact(kw, a.nbytes) and _margins_intact(ww, wsb)
-    assert np.array_equal(kin.cpu().numpy().view(np.int32), np.sort(a))
+    assert np.array_equal(kin.cpu().numpy().view(np.int32), oracle_sorted(a))
 
 
 def test_segmented_sort_stays_inside_its_buffers():

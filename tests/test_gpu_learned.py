@@ -23,15 +23,22 @@ def _sorted_sample(n, seed):
     return x, np.float32(mu), np.float32(sigma)
 
 
+def _normalised_f32(x, mu, sigma):
+    """The normalised keys exactly as the float32 kernels form them: fl(fl(x - mu) / sigma)."""
+    return (x.astype(np.float32) - np.float32(mu)) / np.float32(sigma)
+
+
 def _grad_case(x, mu, sigma, seed, noise):
+    """GPU loss and gradient, and the float64 reference evaluated at the same float32-rounded
+    normalised keys (mu = 0, sigma = 1 on the already normalised points)."""
     rng = np.random.default_rng(seed)
     theta = (L.init_theta(x.astype(np.float64), float(mu), float(sigma)) + rng.normal(0, noise, 48))
     theta = theta.astype(np.float32)
     t = ((np.arange(x.size) + 0.5) / x.size).astype(np.float32)
     loss_gpu, g_gpu = pdq.pdq_learned_loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(),
                                                 theta, float(mu), float(sigma))
-    loss_ref, g_ref = L.loss_grad(theta.astype(np.float64), x.astype(np.float64), t.astype(np.float64),
-                                  float(mu), float(sigma))
+    xn = _normalised_f32(x, mu, sigma).astype(np.float64)
+    loss_ref, g_ref = L.loss_grad(theta.astype(np.float64), xn, t.astype(np.float64), 0.0, 1.0)
     return loss_gpu, np.array(g_gpu), loss_ref, g_ref
 
 
@@ -46,15 +53,16 @@ def test_gradient_parity_with_reference(seed):
     assert np.linalg.norm(g_gpu - g_ref) <= 1e-4 * max(1e-3, np.linalg.norm(g_ref))
 
 
-@pytest.mark.parametrize("seed", range(2))
+@pytest.mark.parametrize("seed", range(4))
 def test_gradient_parity_on_mixture(seed):
-    """On the mixture some ramps are very steep (clusters of width 1e-2 in a range of ~1e4), so a
-    float32 rounding of the normalised key moves it by a visible fraction of such a ramp; the
-    bound is correspondingly looser (1e-2 relative in norm)."""
+    """On the mixture some ramps are very steep (clusters of width 1e-2 in a range of ~1e4), so
+    the float32 rounding of a normalised key moves it by a visible fraction of such a ramp.  The
+    reference therefore takes the same rounded normalised keys the kernels form; everything after
+    that rounding must agree with the float64 reference to 1e-4 relative."""
     x, mu, sigma = _sorted_sample(8192, 10 + seed)
     loss_gpu, g_gpu, loss_ref, g_ref = _grad_case(x, mu, sigma, seed, 0.1)
-    assert abs(loss_gpu - loss_ref) <= 1e-3 * max(1e-3, abs(loss_ref))
-    assert np.linalg.norm(g_gpu - g_ref) <= 1e-2 * max(1e-3, np.linalg.norm(g_ref))
+    assert abs(loss_gpu - loss_ref) <= 1e-4 * max(1e-3, abs(loss_ref))
+    assert np.linalg.norm(g_gpu - g_ref) <= 1e-4 * max(1e-3, np.linalg.norm(g_ref))
 
 
 def test_training_lowers_the_loss_and_folds_consistently():

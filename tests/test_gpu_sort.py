@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import workloads
-from gpu_helpers import bits, gpu_sort
+from gpu_helpers import bits, gpu_sort, oracle_sorted
 
 pytestmark = pytest.mark.gpu
 
@@ -19,10 +19,6 @@ DTYPES = [np.int32, np.uint32, np.int64, np.uint64, np.float32]
 SIZES = [0, 1, 2, 3, 31, 32, 33, 255, 256, 257, 8191, 8192, 8193, 8194, 65537, 300001]
 
 
-def oracle_sorted(a):
-    b = a.copy()
-    oracle.pdqsort(b)
-    return b
 
 
 def keys_for(dtype, n, seed):
@@ -100,7 +96,9 @@ def test_pairs_through_fallback_and_levels(tuning):
     keys = workloads.pattern("dupsq", n, 9, dtype=np.int32)
     vals = np.arange(n, dtype=np.uint32)
     gk, gv, _ = gpu_sort(keys, vals, tuning=tuning)
-    assert np.array_equal(gk, np.sort(keys))
+    ok, ov = keys.copy(), vals.copy()
+    oracle.pdqsort_pairs(ok, ov)
+    assert np.array_equal(gk, ok)
     assert np.array_equal(keys[gv.astype(np.int64)], gk)
     assert np.array_equal(np.sort(gv), vals)
 
@@ -134,7 +132,7 @@ def test_sorted_exit_and_reverse():
     # non-increasing with equal runs is reversed too (unstable order is allowed)
     steps = (np.arange(n)[::-1] // 7).astype(np.int32)
     got, _, st = gpu_sort(steps)
-    assert np.array_equal(got, np.sort(steps)) and st["reversed"] == 1
+    assert np.array_equal(got, oracle_sorted(steps)) and st["reversed"] == 1
 
 
 def test_equal_keys_are_final_after_one_level():
@@ -143,7 +141,7 @@ def test_equal_keys_are_final_after_one_level():
     n = 1 << 20
     a = workloads.pattern("mod16", n, 2, dtype=np.int32)
     got, _, st = gpu_sort(a)
-    assert np.array_equal(got, np.sort(a))
+    assert np.array_equal(got, oracle_sorted(a))
     assert st["passes"] == 1 and st["equal_buckets"] == 16 and st["base_buckets"] == 0
 
 
@@ -152,7 +150,7 @@ def test_few_distinct_passes_bounded(k):
     n = 300000
     a = (workloads.splitmix64(11, n) % np.uint64(k)).astype(np.int64) * 1000003
     got, _, st = gpu_sort(a, tuning=dict(log2_buckets=1, base_capacity=256))
-    assert np.array_equal(got, np.sort(a))
+    assert np.array_equal(got, oracle_sorted(a))
     assert st["passes"] <= k
 
 
@@ -160,7 +158,7 @@ def test_fallback_when_budget_is_zero():
     n = 50000
     a = workloads.pattern("random", n, 8, dtype=np.int32)
     got, _, st = gpu_sort(a, tuning=dict(bad_allowed=-1, base_capacity=256))
-    assert np.array_equal(got, np.sort(a))
+    assert np.array_equal(got, oracle_sorted(a))
     assert st["fallback_buckets"] == 1 and st["passes"] == 0
 
 
@@ -244,10 +242,7 @@ def test_nearly_sorted_clustered_displacements(kind):
             a[s0:s0 + 6] = np.concatenate([a[s0 + 3:s0 + 6], a[s0:s0 + 3]])
     a = a.astype(np.int32)
     got, _, st = gpu_sort(a, tuning=FIXUP)
-    assert np.array_equal(got, np.sort(a))
-    want = a.copy()
-    oracle.pdqsort(want)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got, oracle_sorted(a))
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.uint64])
@@ -262,7 +257,7 @@ def test_nearly_sorted_fixup_on_misaligned_subarrays(dtype, lo, hi):
     a = workloads.pattern("asc_swaps", n, workloads.config_seed(82), dtype=np.int64).astype(dtype)
     end = n + hi if hi else n
     want = a.copy()
-    want[lo:end] = np.sort(a[lo:end])
+    want[lo:end] = oracle_sorted(a[lo:end])
     d = to_device(a)
     st = pdq.pdq_sort_keys(d[lo:end], key_dtype=CODE[np.dtype(dtype)])
     torch.cuda.synchronize()
@@ -286,7 +281,8 @@ def test_nearly_sorted_huge_segment():
     offs = np.array([0, big, big + 5000], dtype=np.int64)
     got, _, _, rc = gpu_sort_segmented(a, offs)
     assert rc == 0
-    want = np.concatenate([np.sort(a[:big]), np.sort(a[big:])])
+    want = a.copy()
+    oracle.pdqsort_segmented(want, offs)
     assert np.array_equal(got, want)
 
 
@@ -317,3 +313,48 @@ def test_keys_holding_the_sentinel_value(dtype, n, frac):
     idx = gv.astype(np.int64)
     assert np.array_equal(np.sort(idx), np.arange(n))
     assert np.array_equal(bits(a[idx]), bits(gk))
+
+
+# ------------------------------------------------------------ bad-split rule (Sec. 4.1)
+def _big_equality_bin(n, seed):
+    """90% of the keys equal 0, the other 10% are distinct and positive, shuffled.  With two
+    buckets per level the one splitter is 0: the zeros fill the equality bin and every other
+    key lands in the bucket above it."""
+    m = n // 10
+    a = np.zeros(n, dtype=np.int32)
+    a[:m] = np.arange(1, m + 1, dtype=np.int32)
+    return a[workloads.permutation(n, seed)].copy()
+
+
+BAD_ONLY_BY_NONEQUAL = dict(log2_buckets=1, base_capacity=256, bad_allowed=1)
+
+
+def test_bad_split_counts_the_parents_non_equal_keys():
+    """The child above the splitter keeps all of its parent's non-equal keys (10% of the
+    parent): a bad split under the rule "more than 7/8 of the parent's non-equal keys", which the
+    parent's total size (90% of it final in the equality bin) would hide.  With a budget of 1 the
+    child goes straight to the merge-path fallback."""
+    n = 200_000
+    a = _big_equality_bin(n, 131)
+    got, _, st = gpu_sort(a, tuning=BAD_ONLY_BY_NONEQUAL)
+    assert np.array_equal(got, oracle_sorted(a))
+    assert st["bad_splits"] >= 1 and st["fallback_buckets"] >= 1
+    vals = np.arange(n, dtype=np.uint32)
+    gk, gv, st = gpu_sort(a, vals, tuning=BAD_ONLY_BY_NONEQUAL)
+    ok, ov = a.copy(), vals.copy()
+    oracle.pdqsort_pairs(ok, ov)
+    assert np.array_equal(gk, ok) and np.array_equal(a[gv.astype(np.int64)], gk)
+    assert st["bad_splits"] >= 1 and st["fallback_buckets"] >= 1
+
+
+def test_bad_split_rule_in_the_segmented_path():
+    from gpu_helpers import gpu_sort_segmented
+    n = 300_000  # 30 000 non-equal keys per segment: above the largest base-sort size
+    a = np.concatenate([_big_equality_bin(n, 132), _big_equality_bin(n, 133)])
+    offs = np.array([0, n, 2 * n], dtype=np.int64)
+    got, _, st, rc = gpu_sort_segmented(a, offs, tuning=BAD_ONLY_BY_NONEQUAL)
+    assert rc == 0
+    want = a.copy()
+    oracle.pdqsort_segmented(want, offs)
+    assert np.array_equal(got, want)
+    assert st["bad_splits"] >= 2 and st["fallback_buckets"] >= 2
