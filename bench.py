@@ -293,13 +293,39 @@ def run_reference(args, rank: int) -> None:
 
 E2_PATTERNS = ["uniform", "dupsq", "dup8", "mod8", "ones", "sort50", "sort90", "sort99", "organ", "merge",
                "asc", "desc"]
-E2_LOG2N = [10, 13, 16, 19, 22, 24]
+E2_LOG2N = [10, 13, 16, 19, 22, 24, 26, 28]
+E2_ORACLE_MAX = 22  # cells up to 2^22 keys are compared with the oracle element by element
+
+
+def _permutation_on_device(n: int, seed: int) -> np.ndarray:
+    """workloads.permutation computed faster: the same SplitMix64 draws, ranked by a stable
+    device sort (the draws' order decides; ties keep index order, as numpy's stable argsort)."""
+    import torch
+    if n < (1 << 22):
+        return workloads.permutation(n, seed)
+    r = torch.from_numpy(workloads.splitmix64(seed, n).view(np.int64)).cuda()
+    r = r ^ torch.iinfo(torch.int64).min  # unsigned order as signed order
+    return torch.sort(r, stable=True).indices.cpu().numpy()
+
+
+def _multiset_hash(t) -> int:
+    """Order-independent hash of a device int32 array: the sum (mod 2^64) of a 64-bit mix of
+    every key."""
+    import torch
+    x = t.to(torch.int64) & 0xFFFFFFFF
+    x = x * -7046029254386353131  # 0x9E3779B97F4A7C15 as int64; products wrap modulo 2^64
+    x = x ^ (x >> 29)
+    x = x * -4658895280553007687  # 0xBF58476D1CE4E5B9
+    return int(x.sum().item())
 
 
 def bench_e2_sweep(args) -> None:
-    """The paper's evaluation grid (Sec. 6.1 input distributions over a range of sizes), int32
-    keys, normalised like its figures: nanoseconds per (n log2 n).  The oracle is timed on the
-    host on the cells up to 2^16 keys for the same normalisation."""
+    """The paper's evaluation grid (Sec. 6.1 input distributions over 2^10 .. 2^28 keys), int32
+    keys, normalised like its figures: nanoseconds per (n log2 n).  Every cell is checked: up to
+    2^22 keys against the oracle element by element, above that by the sorted property and a
+    multiset hash of input and output.  Each cell also gets the whole-sort roofline (bytes the
+    method moves over its passes, from one profiled call, over the median time).  The oracle is
+    timed on the host on the cells up to 2^16 keys for the same normalisation."""
     import torch
     import paper_2106_05123_gb300 as pdq
     import oracle
@@ -307,8 +333,10 @@ def bench_e2_sweep(args) -> None:
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     ws = torch.empty(pdq.pdq_workspace_bytes(1 << max(E2_LOG2N), pdq.PDQ_I32, 0), dtype=torch.uint8, device="cuda")
+    peak, peak_src = measured_peak_gbs()
     sweep, cpu_cells = {}, []
     total_keys, total_ms = 0, 0.0
+    steps = min(args.steps, 5)
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     l0 = pdq.launch_count()
     sampler.start()
@@ -316,26 +344,44 @@ def bench_e2_sweep(args) -> None:
         sweep[pat] = {}
         for lg in E2_LOG2N:
             n = 1 << lg
-            a = workloads.pattern(pat, n, workloads.config_seed(5), dtype=np.int32)
+            a = workloads.pattern(pat, n, workloads.config_seed(5), dtype=np.int32, perm=_permutation_on_device)
             src = torch.from_numpy(a).cuda()
             work = torch.empty_like(src)
             times = []
-            for it in range(args.warmup + min(args.steps, 5)):
+            for it in range(args.warmup + steps):
                 work.copy_(src)
                 flush.zero_()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                pdq.pdq_sort_keys(work, ws, key_dtype=pdq.PDQ_I32)
+                st = pdq.pdq_sort_keys(work, ws, key_dtype=pdq.PDQ_I32)
                 e1.record()
                 torch.cuda.synchronize()
                 if it >= args.warmup:
                     times.append(e0.elapsed_time(e1))
-            if pat in ("uniform", "dupsq"):
-                assert bool((work[1:] >= work[:-1]).all().item()), "output not sorted"
+            if lg <= E2_ORACLE_MAX:
+                want = a.copy()
+                oracle.pdqsort(want)
+                assert np.array_equal(work.cpu().numpy(), want), f"{pat} 2^{lg}: differs from the oracle"
+                check = "oracle"
+            else:
+                assert bool((work[1:] >= work[:-1]).all().item()), f"{pat} 2^{lg}: output not sorted"
+                assert _multiset_hash(work) == _multiset_hash(src), f"{pat} 2^{lg}: keys changed"
+                check = "sorted+multiset"
+            # whole-sort bytes from one profiled call (histogram re-reads are overhead, not credit)
+            work.copy_(src)
+            pdq.profile_reset()
+            pdq.profile_enable(True)
+            pdq.pdq_sort_keys(work, ws, key_dtype=pdq.PDQ_I32)
+            torch.cuda.synchronize()
+            prof = pdq.profile_read()
+            pdq.profile_enable(False)
+            path_bytes = sum(v[2] for k, v in prof.items() if "count" not in k)
             ms = float(statistics.median(times))
             total_keys += n * len(times)
             total_ms += sum(times)
-            cell = {"gpu_ns_per_nlogn": ms * 1e6 / (n * lg), "gpu_ms": ms}
+            cell = {"gpu_ns_per_nlogn": ms * 1e6 / (n * lg), "gpu_ms": ms, "passes": st["passes"],
+                    "check": check, "path_bytes": path_bytes,
+                    "path_frac": path_bytes / (ms * 1e-3) / 1e9 / peak if ms > 0 else None}
             if lg <= 16:
                 reps = max(1, (1 << 18) // n)
                 t0 = time.perf_counter()
@@ -346,18 +392,21 @@ def bench_e2_sweep(args) -> None:
                 cell["cpu_ns_per_nlogn"] = dt * 1e9 / (n * lg)
                 cpu_cells.append((n, dt))
             sweep[pat][f"2^{lg}"] = cell
+            del src, work
     clocks = sampler.stop()
     launches = pdq.launch_count() - l0
     cpu_keys = sum(n for n, _ in cpu_cells)
     cpu_s = sum(t for _, t in cpu_cells)
     line = {"metric": "Gkeys/s", "value": total_keys / (total_ms * 1e-3) / 1e9, "unit": "Gkeys/s", "n_gpus": 1,
-            "steps": min(args.steps, 5), "warmup": args.warmup, "ms_per_step": total_ms / max(1, min(args.steps, 5)),
+            "steps": steps, "warmup": args.warmup, "ms_per_step": total_ms / max(1, steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": {"workload": "e2_sweep", "description": "Sec. 6.1 input distributions x sizes, int32",
                        "patterns": E2_PATTERNS, "log2_n": E2_LOG2N,
                        "l2": "flushed (512 MiB write) and input restored between sorts"},
-            "sweep": sweep, "roofline": None,
+            "sweep": sweep,
+            "roofline": {"bound": "hbm", "kernel": "whole sort per cell (path_frac)", "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s"},
             "cpu_baseline": {"value": cpu_keys / cpu_s / 1e9 if cpu_s else None, "unit": "Gkeys/s", "cores": 1,
                              "kind": "oracle", "sample": "every pattern at 2^10, 2^13, 2^16 keys"},
             "e2e": None, "clocks": clocks, "gpu_launches": launches}

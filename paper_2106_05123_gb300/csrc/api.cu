@@ -70,6 +70,31 @@ int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void note_launch_count(int extra) { g_launches.fetch_add(extra, std::memory_order_relaxed); }
 
+bool profiling_enabled() { return g_profile.load(std::memory_order_relaxed); }
+
+AuxStreams* aux_streams() {
+  constexpr int kMaxDev = 64;
+  thread_local AuxStreams* sets[kMaxDev] = {};
+  thread_local bool failed[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || failed[dev]) return nullptr;
+  if (!sets[dev]) {
+    AuxStreams* a = new AuxStreams();
+    bool ok = cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < kBaseClasses && ok; ++c) {
+      ok = cudaStreamCreateWithFlags(&a->s[c], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&a->join[c], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      failed[dev] = true;
+      return nullptr;  // (the partial set is left to the context's teardown)
+    }
+    sets[dev] = a;
+  }
+  return sets[dev];
+}
+
 GraphCache& graph_cache() {
   static GraphCache* gc = new GraphCache();  // lives until exit (graph objects are host-side)
   return *gc;

@@ -151,6 +151,17 @@ void note_launch_end(const char* name, cudaStream_t s);              // after a 
 int64_t launches_so_far();
 void note_launch_count(int extra);                                   // kernels inside a graph launch
 
+// Streams and events that let the base-sort size classes of one level run concurrently: the
+// calling stream forks to one auxiliary stream per class and joins them again.  One set per host
+// thread and device, created on first use (nullptr if creation failed: run serially).
+struct AuxStreams {
+  cudaStream_t s[kBaseClasses];
+  cudaEvent_t fork;
+  cudaEvent_t join[kBaseClasses];
+};
+AuxStreams* aux_streams();
+bool profiling_enabled();  // per-kernel event timing is on: launches stay serial on their stream
+
 struct LaunchScope {
   const char* name;
   cudaStream_t s;

@@ -4,13 +4,13 @@
 //   probe_kernel      - descents / ascents / min / max over neighbours: the sorted and
 //                       reverse-sorted exits (Sec. 5.2)
 //   reverse_kernel    - in-place reversal for non-increasing input (Sec. 5.2)
-//   sample_kernel     - splitter selection from a hashed sample, sorted in shared memory; a
+//   sample_kernel     - splitter selection from a hashed sample, sorted on chip; a
 //                       multi-way generalisation of median-of-k pivots (Sec. 2) with fresh
 //                       samples per attempt (Sec. 4.2)
 //   count_kernel      - branchless classification of every key into 2B bins: bin 2b holds keys
 //                       strictly between splitters b-1 and b, bin 2b+1 keys equal to splitter b
 //                       (the equal-key rule of Sec. 3)
-//   scan_kernel       - bucket offsets per (chunk, bin)
+//   scan_totals_kernel - bucket starts per task; per-bin cursors the scatter reserves runs from
 //   scatter_kernel    - re-classifies a tile, ranks keys per bin with shared atomics, stages the
 //                       tile in shared memory grouped by bin and writes contiguous runs
 //                       (the GPU form of block partitioning, Sec. 5.3)
@@ -18,7 +18,9 @@
 //                       more than 7/8 of its parent's non-equal keys is a bad split and
 //                       decrements the subtree's counter; at 0 the bin goes to the fallback
 //                       (Sec. 4.1)
-//   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1)
+//   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1): all-equal buckets are
+//                       copied, narrow code ranges take stable LSD counting passes, wide ones a
+//                       register-blocked merge sort
 //   copy_plan_kernel, copy_kernel - final buckets left in the temp buffer go home, decoded, in
 //                       tiles spread over all such buckets
 //   merge_tile_kernel - tiled merge-path merge (the O(n log n) fallback's passes, Sec. 4.1, and
@@ -114,6 +116,36 @@ __device__ void block_exclusive_scan(const uint32_t* in, uint32_t* out, int nbin
     }
   }
   __syncthreads();
+}
+
+// Exclusive block scan of one 32-bit value per thread; *total receives the sum (all threads).
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_sum(uint32_t v, uint32_t* wtmp /* >= THREADS/32 */,
+                                                        uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = THREADS / 32;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (NW == 1) {
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+  }
+  if (lane == 31) wtmp[warp] = x;
+  __syncthreads();
+  uint32_t w = lane < NW ? wtmp[lane] : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+    if (lane >= o) w += y;
+  }
+  *total = __shfl_sync(0xffffffffu, w, NW - 1);
+  const uint32_t before = __shfl_sync(0xffffffffu, w, warp > 0 ? warp - 1 : 0);
+  __syncthreads();  // wtmp may be reused by the caller
+  return x - v + (warp > 0 ? before : 0u);
 }
 
 // ================================================================== probe (Sec. 5.2)
@@ -375,52 +407,90 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
   const U* src = (t.buf == kBufKeys ? keys : tmp) + t.begin;
   const uint64_t seed = mix64((uint64_t)t.begin * 0x9E3779B97F4A7C15ull ^ mix64((uint64_t)t.size) ^
                               ((uint64_t)t.attempt << 48));
-  constexpr int PER = (kMaxSamples + THREADS - 1) / THREADS;
-  U xs[PER];  // all of a thread's sample loads in flight at once
+  static_assert(THREADS * 4 == kMaxSamples, "four samples per thread");
+  const int tid = threadIdx.x, lane = tid & 31;
+  // thread tid holds sample slots 4 tid .. 4 tid + 3; slots at or past ns hold the largest code,
+  // so the first ns slots of the sorted 4096 are the sorted sample
+  U v[4];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int j = threadIdx.x + r * THREADS;
-    xs[r] = U(0);
+  for (int e = 0; e < 4; ++e) {
+    const int j = 4 * tid + e;
+    v[e] = ~U(0);
     if (j < ns) {
       const uint64_t h = mix64(seed + (uint64_t)(j + 1) * 0x9E3779B97F4A7C15ull);
-      xs[r] = src[(int64_t)(h % (uint64_t)t.size)];
+      v[e] = src[(int64_t)__umulhi((uint32_t)(h >> 32), (uint32_t)t.size)];  // uniform in [0, size)
     }
   }
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int j = threadIdx.x + r * THREADS;
-    if (j < ns) s[j] = t.enc ? xs[r] : Key<KT>::enc(xs[r]);
+  for (int e = 0; e < 4; ++e) {
+    if (4 * tid + e < ns && !t.enc) v[e] = Key<KT>::enc(v[e]);
   }
-  __syncthreads();
-  // bitonic sort of s[0..ns), ns a power of two.  A layer of distance j <= 32 pairs elements of
-  // one aligned 64-element block, and a warp's 32 consecutive q cover exactly such blocks, so
-  // between two such layers a warp barrier suffices.
-  for (int k = 2; k <= ns; k <<= 1) {
+  // Bitonic network over 4096 slots: slot i meets i ^ j; the lower slot keeps the smaller code
+  // when (i & k) == 0, the larger otherwise.  Distances below 4 stay in a thread's registers,
+  // below 128 they cross lanes of a warp by shuffle, and from 128 up they go through shared
+  // memory (15 of the 78 layers).
+  auto keep = [](U mine, U other, bool lower, bool up) {
+    const U lo = mine < other ? mine : other, hi = mine < other ? other : mine;
+    return lower == up ? lo : hi;
+  };
+#pragma unroll
+  for (int k = 2; k <= kMaxSamples; k <<= 1) {
+#pragma unroll
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int q = threadIdx.x; q < ns / 2; q += THREADS) {
-        const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));  // j is a power of two
-        const int l = i + j;
-        const bool up = (i & k) == 0;
-        const U a = s[i], b = s[l];
-        if ((a > b) == up) { s[i] = b; s[l] = a; }
+      if (j < 4) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = e ^ j;
+          if (p > e) {
+            const bool up = ((4 * tid + e) & k) == 0;
+            const U a = v[e], b = v[p];
+            const bool sw = (a > b) == up;
+            v[e] = sw ? b : a;
+            v[p] = sw ? a : b;
+          }
+        }
+      } else if (j < 128) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 4 * tid + e;
+          const U o = __shfl_xor_sync(0xffffffffu, v[e], j >> 2);
+          v[e] = keep(v[e], o, (i & j) == 0, (i & k) == 0);
+        }
+      } else {
+        __syncthreads();  // the previous exchange's reads are done
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[4 * tid + e] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 4 * tid + e;
+          v[e] = keep(v[e], s[i ^ j], (i & j) == 0, (i & k) == 0);
+        }
       }
-      const int jn = j > 1 ? j >> 1 : k;  // distance of the next layer
-      if (j <= 32 && jn <= 32) __syncwarp(); else __syncthreads();
     }
   }
+  (void)lane;
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < 4; ++e) s[4 * tid + e] = v[e];
   __syncthreads();
   U* tree = tree_out + (size_t)blockIdx.x * kBMax;
   U* spl = spl_out + (size_t)blockIdx.x * kBMax;
   const int step = ns / B;
-  for (int i = threadIdx.x; i < B - 1; i += THREADS) spl[i] = s[(i + 1) * step - 1];
-  for (int j = 1 + threadIdx.x; j < B; j += THREADS) tree[j] = s[(eytz_inorder(j, logb) + 1) * step - 1];
-  // prefilter table over [spl[0], spl[B-2]] (the splitter of rank i is s[(i + 1) * step - 1])
+  __shared__ U s_spl[kBMax];
+  for (int i = tid; i < B - 1; i += THREADS) {
+    const U x = s[(i + 1) * step - 1];
+    spl[i] = x;
+    s_spl[i] = x;
+  }
+  for (int j = 1 + tid; j < B; j += THREADS) tree[j] = s[(eytz_inorder(j, logb) + 1) * step - 1];
+  // prefilter table over [spl[0], spl[B-2]]
   const U lo = s[step - 1], hi = s[(B - 1) * step - 1];
   const U range = hi - lo;
   const int bits = range == 0 ? 0 : (int)(8 * sizeof(U)) - (sizeof(U) == 4 ? __clz((uint32_t)range) : __clzll((uint64_t)range));
   const int shift = bits > pref_bits<U>() ? bits - pref_bits<U>() : 0;
   const int nent = (int)(range >> shift) + 1;
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     Pref<U> pf;
     pf.lo = lo;
     pf.hi = hi;
@@ -428,21 +498,33 @@ sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_l
     pf.nent = nent;
     pref_out[blockIdx.x] = pf;
   }
+  // Slice k covers the codes lo + [k << shift, (k + 1) << shift) (the last one ends at hi).  A
+  // splitter lies below every code of slice k exactly when its own slice is below k, so with
+  // hist[k] = #splitters in slice k, b_lo(k) = #splitters < first code of k = sum of hist below
+  // k, and hist[k] is the number of candidates inside the slice.
+  __syncthreads();  // every read of the sorted sample is done: its array becomes the histogram
+  uint32_t* hist = reinterpret_cast<uint32_t*>(s);
+  static_assert(sizeof(s) >= sizeof(uint32_t) * 4096, "histogram fits the sample array");
+#pragma unroll
+  for (int e = 0; e < 4; ++e) hist[4 * tid + e] = 0u;
+  __syncthreads();
+  for (int i = tid; i < B - 1; i += THREADS) atomicAdd(&hist[(uint32_t)((s_spl[i] - lo) >> shift)], 1u);
+  __syncthreads();
+  uint32_t c[4], sum = 0u;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    c[e] = hist[4 * tid + e];
+    sum += c[e];
+  }
+  __shared__ uint32_t s_wtmp[THREADS / 32];
+  uint32_t total;
+  uint32_t run = block_exclusive_sum<THREADS>(sum, s_wtmp, &total);
   PrefEnt* tab = tab_out + (size_t)blockIdx.x * pref_entries<U>();
-  for (int k = threadIdx.x; k < nent; k += THREADS) {
-    const U first = lo + ((U)k << shift);
-    const U last = k == nent - 1 ? hi : first + (((U)1 << shift) - 1);
-    int a = 0, c = B - 1;  // #splitters < first: lower bound over spl[0..B-2]
-    while (a < c) {
-      const int m = (a + c) >> 1;
-      if (s[(m + 1) * step - 1] < first) a = m + 1; else c = m;
-    }
-    int a2 = 0, c2 = B - 1;  // #splitters <= last: upper bound
-    while (a2 < c2) {
-      const int m = (a2 + c2) >> 1;
-      if (s[(m + 1) * step - 1] <= last) a2 = m + 1; else c2 = m;
-    }
-    tab[k] = (uint32_t)a | (a2 == a + 1 ? kPrefOne : 0u) | (a2 > a + 1 ? kPrefMany : 0u);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int k = 4 * tid + e;
+    if (k < nent) tab[k] = run | (c[e] == 1u ? kPrefOne : 0u) | (c[e] > 1u ? kPrefMany : 0u);
+    run += c[e];
   }
 }
 
@@ -519,12 +601,13 @@ struct BinSlot {
 // into STAGES shared buffers by bulk copy; elements of a window outside the chunk are masked
 // (only the first and last window have any), and the last window's sub-16-byte tail is
 // classified straight from global memory.  Every code is classified and counted in a shared
-// histogram, written to counts[chunk][bin] at the end.
+// histogram, written to counts[chunk][bin] at the end and added to the task's bin totals.
 template <int KT, class CLS, int THREADS, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
              const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
-             typename CLS::Params cp, uint32_t* __restrict__ counts, int bin_stride, Counters* ctr) {
+             typename CLS::Params cp, uint32_t* __restrict__ counts, int bin_stride,
+             uint32_t* __restrict__ totals, Counters* ctr) {
   using U = typename Key<KT>::U;
   constexpr int KS = sizeof(U);
   constexpr int VEC = 16 / KS;                // codes per 16-byte vector
@@ -625,99 +708,36 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   }
   __syncthreads();
   uint32_t* out = counts + (size_t)blockIdx.x * bin_stride;
-  for (int b = threadIdx.x; b < nb; b += THREADS) out[b] = hist[slot(b)];
+  uint32_t* tot = totals + (size_t)c.task * bin_stride;
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    const uint32_t v = hist[slot(b)];
+    out[b] = v;
+    if (v) atomicAdd(tot + b, v);
+  }
 }
 
 // ================================================================== scan
-// One CTA per task: bin totals over the task's chunks, bin starts, and per-chunk write offsets
-// (relative to the task's first element), written over the counts.  Child (start, size) pairs
-// go to children[task * bin_stride + bin].
+// One CTA per task: the exclusive scan of the task's bin totals gives every bin's first element
+// (relative to the task's first element); children[task * bin_stride + bin] = (start, size), and
+// the totals become the bins' write cursors, from which every scatter CTA reserves the run of
+// its chunk with one atomic per bin.  (Runs of different chunks land in a bin in the order of
+// their reservations: the sort is unstable, so any order is correct.)
 template <int THREADS, int MAXBINS>
 __global__ void __launch_bounds__(THREADS)
-scan_kernel(const int32_t* __restrict__ task_nbins, const int32_t* __restrict__ task_chunk0,
-            const int32_t* __restrict__ task_nchunks, uint32_t* __restrict__ counts, int bin_stride,
-            uint2* __restrict__ children) {
+scan_totals_kernel(const int32_t* __restrict__ task_nbins, uint32_t* __restrict__ totals, int bin_stride,
+                   uint2* __restrict__ children) {
   __shared__ uint32_t tot[MAXBINS];
   __shared__ uint32_t start[MAXBINS];
   __shared__ uint32_t wtmp[THREADS / 32 + 1];
   const int task = blockIdx.x;
   const int nb = task_nbins[task];
-  const int c0 = task_chunk0[task], nc = task_nchunks[task];
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    uint32_t s = 0;
-    for (int c = 0; c < nc; ++c) s += counts[(size_t)(c0 + c) * bin_stride + b];
-    tot[b] = s;
-  }
+  uint32_t* t = totals + (size_t)task * bin_stride;
+  for (int b = threadIdx.x; b < nb; b += THREADS) tot[b] = t[b];
   __syncthreads();
   block_exclusive_scan<THREADS>(tot, start, nb, wtmp);
   for (int b = threadIdx.x; b < nb; b += THREADS) {
-    uint32_t run = start[b];
-    for (int c = 0; c < nc; ++c) {
-      uint32_t* p = counts + (size_t)(c0 + c) * bin_stride + b;
-      const uint32_t v = *p;
-      *p = run;
-      run += v;
-    }
     children[(size_t)task * bin_stride + b] = make_uint2(start[b], tot[b]);
-  }
-}
-
-// Chunk-parallel form of the scan for one task with many chunks (the first level): groups of
-// `per` consecutive chunks are summed per bin by separate CTAs (scan_group_sum_kernel), one CTA
-// turns the group sums into group bases and the task's bin starts (scan_group_base_kernel), and
-// the group CTAs then write every chunk's offsets (scan_group_apply_kernel).  `part` holds
-// groups x bin_stride words.
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-scan_group_sum_kernel(const uint32_t* __restrict__ counts, int bin_stride, int nb, int nc, int per,
-                      uint32_t* __restrict__ part) {
-  const int g = blockIdx.x;
-  const int c0 = g * per, c1 = c0 + per < nc ? c0 + per : nc;
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    uint32_t s = 0;
-    for (int c = c0; c < c1; ++c) s += counts[(size_t)c * bin_stride + b];
-    part[(size_t)g * bin_stride + b] = s;
-  }
-}
-
-template <int THREADS, int MAXBINS>
-__global__ void __launch_bounds__(THREADS)
-scan_group_base_kernel(uint32_t* __restrict__ part, int bin_stride, int nb, int groups, uint2* __restrict__ children) {
-  __shared__ uint32_t tot[MAXBINS];
-  __shared__ uint32_t start[MAXBINS];
-  __shared__ uint32_t wtmp[THREADS / 32 + 1];
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    uint32_t run = 0;
-    for (int g = 0; g < groups; ++g) {
-      uint32_t* p = part + (size_t)g * bin_stride + b;
-      const uint32_t v = *p;
-      *p = run;  // exclusive prefix over the groups
-      run += v;
-    }
-    tot[b] = run;
-  }
-  __syncthreads();
-  block_exclusive_scan<THREADS>(tot, start, nb, wtmp);
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    for (int g = 0; g < groups; ++g) part[(size_t)g * bin_stride + b] += start[b];
-    children[b] = make_uint2(start[b], tot[b]);
-  }
-}
-
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS)
-scan_group_apply_kernel(uint32_t* __restrict__ counts, int bin_stride, int nb, int nc, int per,
-                        const uint32_t* __restrict__ part) {
-  const int g = blockIdx.x;
-  const int c0 = g * per, c1 = c0 + per < nc ? c0 + per : nc;
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    uint32_t run = part[(size_t)g * bin_stride + b];
-    for (int c = c0; c < c1; ++c) {
-      uint32_t* p = counts + (size_t)c * bin_stride + b;
-      const uint32_t v = *p;
-      *p = run;
-      run += v;
-    }
+    t[b] = start[b];
   }
 }
 
@@ -734,7 +754,8 @@ __global__ void __launch_bounds__(THREADS, 2)  // two resident CTAs per SM: at m
 scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
                typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
                typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv,
-               typename CLS::Params cp, const uint32_t* __restrict__ offsets, int bin_stride, Counters* ctr) {
+               typename CLS::Params cp, const uint32_t* __restrict__ counts, int bin_stride,
+               uint32_t* __restrict__ cursors, Counters* ctr) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
   constexpr int KS = sizeof(U);
@@ -762,8 +783,9 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   const Task t = tasks[c.task];
   const int nb = CLS::setup(cs, cp, c.task);
   const BinSlot<CLS::kEqualBins> slot{__ffs(nb) - 2};  // hist, cursor, gbase and stage_b hold slots
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    cursor[slot(b)] = offsets[(size_t)blockIdx.x * bin_stride + b];
+  for (int b = threadIdx.x; b < nb; b += THREADS) {  // reserve this chunk's run in every bin
+    const uint32_t cnt = counts[(size_t)blockIdx.x * bin_stride + b];
+    cursor[slot(b)] = cnt ? atomicAdd(cursors + (size_t)c.task * bin_stride + b, cnt) : 0u;
     hist[b] = 0;
   }
   if (threadIdx.x == 0) {
@@ -1075,6 +1097,114 @@ __device__ __forceinline__ void register_sort(U (&k)[N], uint32_t (&x)[N]) {
   }
 }
 
+// Shared bytes of the base sort's key, position and value arrays (the radix counters follow).
+template <int KS, int VB, int THREADS, int ITEMS>
+__host__ __device__ constexpr size_t base_sort_core_smem() {
+  return ((size_t)base_sort_pcap<KS>(THREADS * ITEMS, ITEMS) * (KS + (VB ? 4 : 0)) + (size_t)THREADS * ITEMS * VB +
+          15) / 16 * 16;
+}
+
+// ------------------------------------------------------------------ range-aware radix base case
+// After the distribution levels a bucket holds the keys between two neighbouring splitters, so
+// its codes usually span a narrow range [mn, mx].  Such a bucket is sorted by a stable LSD
+// counting sort on r = code - mn (at most kRadixMaxBits bits): ceil(bits / kRadixDigitBits)
+// passes over equal-width digits, every pass ranking the keys in shared memory.
+//
+// Ranking (one pass): thread t holds ITEMS consecutive keys (blocked).  Each thread counts its
+// own keys per digit in 16-bit counters, two digits packed in one 32-bit word: digit d counts
+// in word (d mod LW) * THREADS + t, low half for d < LW, high half above (LW = half the digit
+// count).  A thread's counters all sit in the bank of its lane, so the counting is free of
+// bank conflicts.  The words are then scanned in their linear order (digit-major, thread-minor),
+// which is exactly the order of the stable ranks: each thread rakes LW + 1 consecutive words (an
+// odd stride: conflict-free), a block scan joins the rakes, and one packed scan gives the
+// prefixes of the low digits in the low halves and of the high digits in the high halves; the
+// high digits then add the count of all low digits.  A key's destination is its digit-thread
+// prefix plus the number of the thread's earlier keys with that digit.  The (LW+1)-th word of
+// every raking segment is padding that is never counted.
+constexpr int kRadixDigitBits = 6;                 // at most 64 digits per pass
+constexpr int kRadixLanes = 1 << (kRadixDigitBits - 1);
+constexpr int kRadixMaxBits = 24;                  // wider ranges use the merge-path base sort
+
+template <int THREADS>
+__host__ __device__ constexpr size_t radix_counter_bytes() {
+  return (size_t)(kRadixLanes + 1) * THREADS * sizeof(uint32_t);
+}
+
+// The radix path is compiled in where its counters fit next to the base sort's arrays in the
+// 227 KiB a CTA may use (all classes but the largest ones with values).
+template <int KS, int VB, int THREADS, int ITEMS>
+__host__ __device__ constexpr bool radix_fits() {
+  return base_sort_core_smem<KS, VB, THREADS, ITEMS>() + radix_counter_bytes<THREADS>() <= (size_t)227 * 1024;
+}
+
+// Sorts the active threads' keys r[0..ITEMS) (and positions x, when W) by LSD passes over
+// `nbits` <= 24 bits.  Real keys are below 2^24; padding keys are 0xFFFFFF and stay behind every
+// real key (stable ranks, padding last in the input).  Bits 24-31 of r carry, within a pass, the
+// key's rank among its thread's earlier keys of the same digit.  On return arr[pad(i)] (and
+// idx[pad(i)]) hold the sorted sequence for i < P.  ctr: radix_counter_bytes<THREADS>().
+template <int THREADS, int ITEMS, bool W>
+__device__ __forceinline__ void radix_block_sort(uint32_t (&r)[ITEMS], uint32_t (&x)[ITEMS], bool active,
+                                                 int nbits, uint32_t* __restrict__ arr, uint32_t* __restrict__ idx,
+                                                 uint32_t* __restrict__ ctr, uint32_t* wtmp) {
+  constexpr int LW = kRadixLanes;
+  constexpr int SEG = LW + 1;
+  const int tid = threadIdx.x;
+  const int passes = (nbits + kRadixDigitBits - 1) / kRadixDigitBits;
+  const int w = (nbits + passes - 1) / passes;
+  const uint32_t dmask = (1u << w) - 1u;
+  auto pad = [](int i) { return i + (i >> 5); };
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * w;
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) ctr[tid * SEG + j] = 0u;
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        const uint32_t d = (r[e] >> shift) & dmask;
+        const uint32_t sh = (d & LW) ? 16u : 0u;
+        uint32_t* c = ctr + (d & (LW - 1)) * THREADS + tid;
+        const uint32_t v = *c;
+        r[e] = (r[e] & 0xFFFFFFu) | (((v >> sh) & 0xFFu) << 24);
+        *c = v + (1u << sh);
+      }
+    }
+    __syncthreads();
+    uint32_t sum = 0u;  // the raking segment is read twice rather than held in registers
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) sum += ctr[tid * SEG + j];
+    uint32_t total;
+    uint32_t run = block_exclusive_sum<THREADS>(sum, wtmp, &total);
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      const uint32_t v = ctr[tid * SEG + j];
+      ctr[tid * SEG + j] = run;
+      run += v;
+    }
+    const uint32_t low_total = total & 0xFFFFu;  // keys whose digit is below LW
+    __syncthreads();
+    // every thread's keys are in its registers, so the array can be overwritten at once
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        const uint32_t d = (r[e] >> shift) & dmask;
+        const uint32_t v = ctr[(d & (LW - 1)) * THREADS + tid];
+        const int dst = (int)(((d & LW) ? (v >> 16) + low_total : (v & 0xFFFFu)) + (r[e] >> 24));
+        arr[pad(dst)] = r[e] & 0xFFFFFFu;
+        if (W) idx[pad(dst)] = x[e];
+      }
+    }
+    __syncthreads();  // the array is complete and every counter read before the next clear
+    if (active && pass + 1 < passes) {
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        r[e] = arr[pad(tid * ITEMS + e)];
+        if (W) x[e] = idx[pad(tid * ITEMS + e)];
+      }
+    }
+  }
+}
+
 // The whole sort of one item by one CTA (blockDim.x == THREADS); `smem` holds
 // base_sort_smem<KS, VB, THREADS, ITEMS>() bytes, 16-byte aligned.
 template <int KT, int VB, int THREADS, int ITEMS>
@@ -1101,16 +1231,46 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   const U* srck = (it.buf == kBufKeys ? keys : tmpk) + it.begin;
   const V* srcv = W ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
   bool max_code = false;  // a real code equal to the sentinel value (all ones)
-  for (int i = tid; i < P + ITEMS; i += THREADS) {  // ITEMS slack slots: harmless read-ahead
-    U c = ~U(0);
-    if (i < m) {
-      const U x = srck[i];
-      c = it.enc ? x : Key<KT>::enc(x);
-      max_code |= c == ~U(0);
-      if (W) sv[i] = srcv[i];
+  U mn = ~U(0), mx = U(0);  // range of the real codes
+  // Staging: slots [0, P + ITEMS) (ITEMS slack slots: harmless read-ahead of the merge) are
+  // covered by ITEMS + 1 strided slots per thread, as CAP + THREADS >= P + ITEMS.  All of a
+  // thread's global loads are issued before any is used, so their latency is paid once.
+  {
+    U xk[ITEMS + 1];
+    V xv[W ? ITEMS + 1 : 1];
+#pragma unroll
+    for (int e = 0; e <= ITEMS; ++e) {
+      const int i = tid + e * THREADS;
+      xk[e] = ~U(0);
+      if (i < m) {
+        xk[e] = srck[i];
+        if (W) xv[W ? e : 0] = srcv[i];
+      }
     }
-    sk[pad_idx<U>(i)] = c;
-    if (W) si[pad_idx<U>(i)] = (uint32_t)i;
+#pragma unroll
+    for (int e = 0; e <= ITEMS; ++e) {
+      const int i = tid + e * THREADS;
+      U c = ~U(0);
+      if (i < m) {
+        c = it.enc ? xk[e] : Key<KT>::enc(xk[e]);
+        max_code |= c == ~U(0);
+        mn = c < mn ? c : mn;
+        mx = c > mx ? c : mx;
+        if (W) sv[i] = xv[W ? e : 0];
+      }
+      if (i < P + ITEMS) {
+        sk[pad_idx<U>(i)] = c;
+        if (W) si[pad_idx<U>(i)] = (uint32_t)i;
+      }
+    }
+  }
+  __shared__ U s_wmn[THREADS / 32], s_wmx[THREADS / 32];
+  __shared__ uint32_t s_wtmp[THREADS / 32];
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  if ((tid & 31) == 0) {
+    s_wmn[tid >> 5] = mn;
+    s_wmx[tid >> 5] = mx;
   }
   // Without a real all-ones code every real key is below the padding and the sentinels, and
   // equal real keys may end in any order (the sort is unstable), so codes alone are compared
@@ -1119,6 +1279,49 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   // original position (CMPIDX true: padding positions are >= m, sentinel indices all ones).
   // (the block-wide OR is also the barrier after the staging writes: always executed)
   const bool any_max = __syncthreads_or(max_code) != 0;
+#pragma unroll 1
+  for (int w = 0; w < THREADS / 32; ++w) {
+    mn = s_wmn[w] < mn ? s_wmn[w] : mn;
+    mx = s_wmx[w] > mx ? s_wmx[w] : mx;
+  }
+  U* dstk = (out_buf == kBufKeys ? keys : tmpk) + it.begin;
+  V* dstv = W ? (out_buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
+  if (mn == mx) {  // every key is equal: the order is the input order (values keep theirs)
+    const U c = decode ? Key<KT>::dec(mn) : mn;
+    for (int i = tid; i < m; i += THREADS) {
+      dstk[i] = c;
+      if (W) dstv[i] = sv[i];
+    }
+    return;
+  }
+  const U span = mx - mn;
+  const int nbits = (int)(8 * sizeof(U)) - (sizeof(U) == 4 ? __clz((uint32_t)span) : __clzll((uint64_t)span));
+  if constexpr (radix_fits<sizeof(U), VB, THREADS, ITEMS>()) {
+   if (nbits <= kRadixMaxBits) {
+    // narrow range: LSD counting passes on r = code - mn (padding r = 0xFFFFFF sorts last)
+    uint32_t* arr = reinterpret_cast<uint32_t*>(sk);
+    uint32_t* ctr = reinterpret_cast<uint32_t*>(smem + base_sort_core_smem<sizeof(U), VB, THREADS, ITEMS>());
+    uint32_t r[ITEMS], xp[ITEMS];
+    const bool act = tid < na;
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < ITEMS; ++e) {
+        const int i = tid * ITEMS + e;
+        r[e] = i < m ? (uint32_t)(sk[pad_idx<U>(i)] - mn) : 0xFFFFFFu;
+        xp[e] = (uint32_t)i;
+      }
+    }
+    __syncthreads();  // the code array is rewritten as 32-bit ranks
+    radix_block_sort<THREADS, ITEMS, W>(r, xp, act, nbits, arr, si, ctr, s_wtmp);
+    for (int i = tid; i < m; i += THREADS) {
+      const int p = i + (i >> 5);
+      const U c = mn + (U)arr[p];
+      dstk[i] = decode ? Key<KT>::dec(c) : c;
+      if (W) dstv[i] = sv[si[p]];
+    }
+    return;
+   }
+  }
   const bool checked = !W && any_max;
   U k[ITEMS];
   uint32_t x[ITEMS];
@@ -1259,8 +1462,6 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
     }
   }
   __syncthreads();
-  U* dstk = (out_buf == kBufKeys ? keys : tmpk) + it.begin;
-  V* dstv = W ? (out_buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
   for (int i = tid; i < m; i += THREADS) {
     const int p = pad_idx<U>(i);
     const U c = sk[p];
@@ -1281,7 +1482,8 @@ base_sort_kernel(const Item* __restrict__ items, typename Key<KT>::U* __restrict
 
 template <int KS, int VB, int THREADS, int ITEMS>
 constexpr size_t base_sort_smem() {
-  return (size_t)base_sort_pcap<KS>(THREADS * ITEMS, ITEMS) * (KS + (VB ? 4 : 0)) + (size_t)THREADS * ITEMS * VB;
+  return base_sort_core_smem<KS, VB, THREADS, ITEMS>() +
+         (radix_fits<KS, VB, THREADS, ITEMS>() ? radix_counter_bytes<THREADS>() : 0);
 }
 
 // ================================================================== copy temp -> keys (decode)

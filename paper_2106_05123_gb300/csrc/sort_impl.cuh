@@ -60,6 +60,8 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
   L.task_meta = take((size_t)L.round_cap * 4 * sizeof(int32_t));
   L.chunks = take((size_t)L.chunk_cap * sizeof(Chunk));
   L.counts = take((size_t)L.chunk_cap * kBinsMax * sizeof(uint32_t));
+  // per-(task, bin) totals, then write cursors (the learned level has one task of 4096 bins)
+  L.totals = take((size_t)std::max<int64_t>(L.round_cap * kBinsMax, 4096) * sizeof(uint32_t));
   L.tree = take((size_t)L.round_cap * kBMax * ks);
   L.spl = take((size_t)L.round_cap * kBMax * ks);
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
@@ -106,7 +108,7 @@ struct Shape {
   // base sort: CAP = THREADS * ITEMS for the size classes 1024, 2048, 4096, 8192 (, 16384 for
   // 4-byte keys with at most 4-byte values: 1024 threads, and the shared memory fits); ITEMS =
   // 32 keys per thread for 4-byte keys alone, 16 otherwise (54-79 registers, no spills)
-  static constexpr int kBaseItems = VB == 0 ? (KS == 4 ? 32 : 16) : 16;
+  static constexpr int kBaseItems = VB == 0 && KS == 4 ? 32 : 16;
   static constexpr int base_threads(int cls) { return (1024 << cls) / kBaseItems; }
   static constexpr int kMaxClass = (KS == 4 && VB <= 4) ? 4 : 3;
   static constexpr int kMaxCap = 1024 << kMaxClass;
@@ -158,6 +160,7 @@ class PlainSorter {
     meta_ = reinterpret_cast<int32_t*>(ws + L_.task_meta);
     chunks_ = reinterpret_cast<Chunk*>(ws + L_.chunks);
     counts_ = reinterpret_cast<uint32_t*>(ws + L_.counts);
+    totals_ = reinterpret_cast<uint32_t*>(ws + L_.totals);
     tree_ = reinterpret_cast<U*>(ws + L_.tree);
     spl_ = reinterpret_cast<U*>(ws + L_.spl);
     children_ = reinterpret_cast<uint2*>(ws + L_.children);
@@ -219,6 +222,7 @@ class PlainSorter {
   int32_t* meta_;
   Chunk* chunks_;
   uint32_t* counts_;
+  uint32_t* totals_;  // per-(task, bin) key totals, turned into write cursors by the scan
   uint2* children_;
   Pref<U>* pref_;
   PrefEnt* tab_;
@@ -339,25 +343,24 @@ class PlainSorter {
       PDQ_CUDA(cudaMemcpyAsync(meta_, meta, sizeof(meta), cudaMemcpyHostToDevice, st_));
       PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
       PDQ_CUDA(cudaMemsetAsync(ctr_, 0, offsetof(Counters, probe), st_));
-      const int32_t* d_c0 = meta_ + 1;
-      const int32_t* d_nc = meta_ + 2;
+      PDQ_CUDA(cudaMemsetAsync(totals_, 0, sizeof(uint32_t) * kLearnedBuckets, st_));
       const int32_t* d_nb = meta_ + 3;
       {
         LaunchScope ls("learned_count", st_, (double)n * KS);
         count_kernel<KT, ModelCls, S::kCountThreads, S::kCountTile, S::kCountStages>
             <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, model, counts_,
-                                                                kLearnedBuckets, ctr_);
+                                                                kLearnedBuckets, totals_, ctr_);
       }
       PDQ_LAUNCHED("learned_count");
       {
         LaunchScope ls("learned_scan", st_, 0.0);
-        scan_kernel<1024, kLearnedBuckets><<<1, 1024, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kLearnedBuckets, children_);
+        scan_totals_kernel<1024, kLearnedBuckets><<<1, 1024, 0, st_>>>(d_nb, totals_, kLearnedBuckets, children_);
       }
       PDQ_LAUNCHED("learned_scan");
       {
         LaunchScope ls("learned_scatter", st_, 2.0 * (double)n * KS);
         scatter_kernel<KT, 0, ModelCls, 512, kLTile><<<nchunks, 512, kLScatterSmem, st_>>>(
-            chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, ctr_);
+            chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, totals_, ctr_);
       }
       PDQ_LAUNCHED("learned_scatter");
       {
@@ -655,6 +658,7 @@ class PlainSorter {
     PDQ_CUDA(cudaMemcpyAsync(meta_, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice, st_));
     PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
     PDQ_CUDA(cudaMemsetAsync(ctr_, 0, offsetof(Counters, probe), st_));
+    PDQ_CUDA(cudaMemsetAsync(totals_, 0, sizeof(uint32_t) * kBinsMax * (size_t)nt, st_));
 
     int oversample = a_.tune.oversample;
     {
@@ -667,31 +671,19 @@ class PlainSorter {
       LaunchScope ls("count", st_, (double)total * KS);
       count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>
           <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, cls_params(d_logb),
-                                                              counts_, kBinsMax, ctr_);
+                                                              counts_, kBinsMax, totals_, ctr_);
     }
     PDQ_LAUNCHED("count");
     {
       LaunchScope ls("scan", st_, 0.0);
-      constexpr int kPer = 8;  // chunks per group of the chunk-parallel scan
-      const int groups = (nchunks + kPer - 1) / kPer;
-      if (nt == 1 && nchunks >= 8 * kPer && (int64_t)nchunks + groups <= L_.chunk_cap) {
-        // one task with many chunks: the per-bin walk over all chunks would run on one CTA
-        uint32_t* part = counts_ + (size_t)nchunks * kBinsMax;  // rows past the used chunks
-        const int nb = meta[3 * nt];
-        scan_group_sum_kernel<256><<<groups, 256, 0, st_>>>(counts_, kBinsMax, nb, nchunks, kPer, part);
-        scan_group_base_kernel<512, kBinsMax><<<1, 512, 0, st_>>>(part, kBinsMax, nb, groups, children_);
-        scan_group_apply_kernel<256><<<groups, 256, 0, st_>>>(counts_, kBinsMax, nb, nchunks, kPer, part);
-        note_launch_count(2);
-      } else {
-        scan_kernel<256, kBinsMax><<<nt, 256, 0, st_>>>(d_nb, d_c0, d_nc, counts_, kBinsMax, children_);
-      }
+      scan_totals_kernel<512, kBinsMax><<<nt, 512, 0, st_>>>(d_nb, totals_, kBinsMax, children_);
     }
     PDQ_LAUNCHED("scan");
     {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
       scatter_kernel<KT, VB, SplitterCls<U>, S::kScatterThreads, S::kScatterTile>
           <<<nchunks, S::kScatterThreads, S::kScatterSmem, st_>>>(
-              chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, ctr_);
+              chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, totals_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
     {
@@ -723,12 +715,33 @@ class PlainSorter {
     if (h.overflow) return set_error(PDQ_ERR_INTERNAL, "bookkeeping list capacity exceeded");
     stats_.equal_buckets += (int64_t)h.equal_buckets;
     stats_.bad_splits += (int64_t)h.bad_splits;
-    // the level's base elements are counted once, on the first class launched
+    // The size classes run concurrently on auxiliary streams forked from the call's stream and
+    // joined back before anything later on it (the next level's bookkeeping rewrites the lists).
+    // The level's base elements are counted once, on the first class launched.
     int64_t base_elems = (int64_t)h.base_elems;
+    int nclasses = 0;
+    for (int cls = 0; cls < kBaseClasses; ++cls) nclasses += h.n_base[cls] ? 1 : 0;
+    // (with per-kernel timing on they stay serial, so that each launch's time is its own)
+    AuxStreams* aux = nclasses > 1 && !profiling_enabled() ? aux_streams() : nullptr;
+    if (aux && cudaEventRecord(aux->fork, st_) != cudaSuccess) aux = nullptr;
+    bool joined[kBaseClasses] = {};
+    auto join_all = [&]() {  // the call's stream waits for every class launched so far
+      for (int cls = 0; cls < kBaseClasses; ++cls)
+        if (joined[cls]) cudaStreamWaitEvent(st_, aux->join[cls], 0);
+    };
     for (int cls = 0; cls < kBaseClasses; ++cls) {
       if (!h.n_base[cls]) continue;
-      int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, base_elems);
-      if (rc) return rc;
+      cudaStream_t s = st_;
+      if (aux) {
+        s = aux->s[cls];
+        if (cudaStreamWaitEvent(s, aux->fork, 0) != cudaSuccess) s = st_;
+      }
+      const int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, base_elems, s);
+      if (s != st_ && cudaEventRecord(aux->join[cls], s) == cudaSuccess) joined[cls] = true;
+      if (rc) {
+        if (aux) join_all();
+        return rc;
+      }
       base_elems = 0;
     }
     if (h.n_copy) {
@@ -745,6 +758,7 @@ class PlainSorter {
       copy_kernel<KT, VB, 256, kCopyTile><<<(unsigned)blocks, 256, 0, st_>>>(
           copy_items_, (int)h.n_copy, tile0, keys_, vals_, tmpk_, tmpv_);
     }
+    if (aux) join_all();
     PDQ_LAUNCHED("copy");
     if (h.n_fallback) {
       std::vector<Item> fb(h.n_fallback);
@@ -768,14 +782,14 @@ class PlainSorter {
   // Base sort of `count` items of size class `cls` (holding `elems` elements for the byte
   // accounting) already in that class's list.
   template <int CLS>
-  int base_sort_cls(int64_t count, int out_buf, int decode, int64_t elems) {
+  int base_sort_cls(int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st) {
     constexpr int T = S::base_threads(CLS);
     constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
     const Item* list = base_items_ + L_.base_off[CLS];
     for (int64_t done = 0; done < count;) {
       const int64_t g = std::min<int64_t>(count - done, 1 << 30);
-      LaunchScope ls("base_sort", st_, done == 0 ? 2.0 * (double)elems * (KS + VB) : 0.0);
-      base_sort_kernel<KT, VB, T, S::kBaseItems><<<(unsigned)g, T, smem, st_>>>(
+      LaunchScope ls("base_sort", st, done == 0 ? 2.0 * (double)elems * (KS + VB) : 0.0);
+      base_sort_kernel<KT, VB, T, S::kBaseItems><<<(unsigned)g, T, smem, st>>>(
           list + done, keys_, vals_, tmpk_, tmpv_, out_buf, decode);
       done += g;
     }
@@ -793,15 +807,16 @@ class PlainSorter {
     note_launch_count(1);
   }
 
-  int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems) {
+  int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st = nullptr) {
     stats_.base_buckets += count;
+    if (!st) st = st_;
     switch (cls) {
-      case 0: return base_sort_cls<0>(count, out_buf, decode, elems);
-      case 1: return base_sort_cls<1>(count, out_buf, decode, elems);
-      case 2: return base_sort_cls<2>(count, out_buf, decode, elems);
-      case 3: return base_sort_cls<3>(count, out_buf, decode, elems);
+      case 0: return base_sort_cls<0>(count, out_buf, decode, elems, st);
+      case 1: return base_sort_cls<1>(count, out_buf, decode, elems, st);
+      case 2: return base_sort_cls<2>(count, out_buf, decode, elems, st);
+      case 3: return base_sort_cls<3>(count, out_buf, decode, elems, st);
       default:
-        if constexpr (S::kMaxClass >= 4) return base_sort_cls<4>(count, out_buf, decode, elems);
+        if constexpr (S::kMaxClass >= 4) return base_sort_cls<4>(count, out_buf, decode, elems, st);
         return set_error(PDQ_ERR_INTERNAL, "base class out of range");
     }
   }

@@ -73,14 +73,19 @@ def permutation(n: int, seed: int) -> np.ndarray:
     return np.argsort(splitmix64(seed, n), kind="stable").astype(np.int64)
 
 
-def shuffle(a: np.ndarray, seed: int) -> np.ndarray:
-    return a[permutation(a.size, seed)]
+def shuffle(a: np.ndarray, seed: int, perm=None) -> np.ndarray:
+    return a[(perm or permutation)(a.size, seed)]
 
 
 # ------------------------------------------------------------------ paper distributions (Sec. 6.1)
-def pattern(name: str, n: int, seed: int, dtype=np.int32) -> np.ndarray:
-    """One named input pattern of n keys."""
+def pattern(name: str, n: int, seed: int, dtype=np.int32, perm=None) -> np.ndarray:
+    """One named input pattern of n keys.  `perm(n, seed)` may replace `permutation` by a
+    faster routine that returns the same permutation (used for very large n)."""
     i = np.arange(n, dtype=np.int64)
+
+    def shuffle(a, seed):
+        return a[(perm or permutation)(a.size, seed)]
+
     if name == "uniform":        # A[i] = i, shuffled
         a = shuffle(i, seed)
     elif name == "random":       # i.i.d. uniform over the dtype's full range
