@@ -395,6 +395,9 @@ class PlainSorter {
     PDQ_CUDA(cudaFuncSetAttribute(base_sort_kernel<KT, VB, T, S::kBaseItems>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)base_sort_smem<KS, VB, T, S::kBaseItems>()));
+    // as many resident CTAs as shared memory allows (the L1 share is of no use to this kernel)
+    PDQ_CUDA(cudaFuncSetAttribute(base_sort_kernel<KT, VB, T, S::kBaseItems>,
+                                  cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared));
     return PDQ_OK;
   }
 
