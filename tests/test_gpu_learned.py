@@ -119,24 +119,62 @@ def test_learned_sort_is_exact_on_hard_inputs(kind):
     assert np.array_equal(bits(got), bits(want))
 
 
-def test_trained_model_gains_over_its_starting_point():
-    """What training buys over the untrained network (ramps on the sixteenths of the sample), on
-    fresh keys of the same mixture: a lower squared error to the empirical CDF, and the share of
-    keys that land in buckets needing the exact repair (more than 4x the mean load)."""
-    x, _, _ = _sorted_sample(1 << 18, 11)
-    out = pdq.pdq_learned_train(torch.from_numpy(x).cuda(), steps=64, batch=16384)
+def _total_order_codes(x: np.ndarray) -> np.ndarray:
+    """float32 keys as unsigned integers in IEEE totalOrder (test-side helper)."""
+    b = x.view(np.uint32).astype(np.uint64)
+    neg = (b >> np.uint64(31)) == 1
+    return np.where(neg, np.uint64(0xFFFFFFFF) - b, b | np.uint64(0x80000000))
+
+
+def test_trained_model_gain_at_equal_sample_budget():
+    """What the trained network buys, on keys of the mixture workload, from one 1% sample:
+    bucket balance (max / mean keys of the 4096 buckets) and CDF error of the trained model
+    against its untrained starting point, with the sampled-splitter method at the same sample
+    budget (4095 sample quantiles) and the device times of both sorts reported beside them.
+    Training must improve on its starting point; the comparison with sampled splitters is
+    measured and printed alongside: the test asserts the CDF gain, the other figures are
+    recorded (on this mixture the splitters balance better and the plain path is faster)."""
+    n, nb = 1 << 22, 4096
+    keys, _ = workloads.mixture_f32(n, 13)
+    m = n // 100
+    pos = (workloads.splitmix64(workloads.substream(13, 7), m) % np.uint64(n)).astype(np.int64)
+    sample = keys[pos].copy()
+    oracle.pdqsort(sample)
+    out = pdq.pdq_learned_train(torch.from_numpy(sample).cuda(), steps=24, batch=32768)
     mu, sigma = out["mu"], out["sigma"]
-    big = np.sort(workloads.mixture_f32(1 << 20, 11)[0]).astype(np.float64)  # same mixture
-    t = (np.arange(big.size) + 0.5) / big.size
-    th0 = L.init_theta(x.astype(np.float64), mu, sigma)
+    fin = sample[np.isfinite(sample)].astype(np.float64)
+    th0 = L.init_theta(fin, mu, sigma)
     th1 = np.array(out["theta"], dtype=np.float64)
 
-    def overflow_fraction(theta):
-        counts = np.bincount(L.buckets(theta, big, mu, sigma), minlength=4096)
-        return counts[counts > 4 * big.size / 4096].sum() / big.size
+    def balance(counts):
+        return counts.max() / (n / nb)
 
-    mse0, mse1 = L.loss(th0, big, t, mu, sigma) / big.size, L.loss(th1, big, t, mu, sigma) / big.size
-    f0, f1 = overflow_fraction(th0), overflow_fraction(th1)
-    print(f"CDF mse: untrained {mse0:.3e}, trained {mse1:.3e}; "
-          f"keys in overflowing buckets: untrained {f0:.4f}, trained {f1:.4f}")
+    b0 = np.bincount(L.buckets(th0, keys, mu, sigma, nb), minlength=nb)
+    b1 = np.bincount(L.buckets(th1, keys, mu, sigma, nb), minlength=nb)
+    codes = _total_order_codes(keys)
+    spl = _total_order_codes(sample)[((np.arange(1, nb) * m) // nb)]
+    bs = np.bincount(np.searchsorted(spl, codes, side="right"), minlength=nb)
+    srt = np.sort(keys[np.isfinite(keys)]).astype(np.float64)
+    t = (np.arange(srt.size) + 0.5) / srt.size
+    mse0 = L.loss(th0, srt, t, mu, sigma) / srt.size
+    mse1 = L.loss(th1, srt, t, mu, sigma) / srt.size
+
+    def device_ms(fn):
+        d = torch.from_numpy(keys).cuda()
+        ts = []
+        for _ in range(4):
+            d.copy_(torch.from_numpy(keys))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(d)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts[1:]))
+
+    t_learned = device_ms(lambda d: pdq.pdq_sort_keys_learned(d))
+    t_plain = device_ms(lambda d: pdq.pdq_sort_keys(d))
+    print(f"max/mean bucket: untrained {balance(b0):.2f}, trained {balance(b1):.2f}, "
+          f"sampled splitters {balance(bs):.2f}; CDF mse untrained {mse0:.3e}, trained {mse1:.3e}; "
+          f"device ms learned {t_learned:.3f}, plain {t_plain:.3f}")
     assert mse1 < mse0
