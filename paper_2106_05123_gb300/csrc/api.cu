@@ -80,7 +80,10 @@ AuxStreams* aux_streams() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || failed[dev]) return nullptr;
   if (!sets[dev]) {
     AuxStreams* a = new AuxStreams();
-    bool ok = cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) == cudaSuccess;
+    bool ok = cudaEventCreateWithFlags(&a->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&a->ready, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&a->copied, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&a->copy, cudaStreamNonBlocking) == cudaSuccess;
     for (int c = 0; c < kBaseClasses && ok; ++c) {
       ok = cudaStreamCreateWithFlags(&a->s[c], cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&a->join[c], cudaEventDisableTiming) == cudaSuccess;
@@ -235,7 +238,8 @@ static size_t dispatch_ws(int dt, int64_t n) {
 }
 
 static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int dt, void* ws,
-                       size_t ws_bytes, void* stream, const pdq_tuning* tuning, pdq_stats* stats) {
+                       size_t ws_bytes, void* stream, const pdq_tuning* tuning, pdq_stats* stats,
+                       void* host_keys = nullptr, void* host_vals = nullptr) {
   g_last_error.clear();
   if (stats) std::memset(stats, 0, sizeof(*stats));
   const int kb = key_bytes(dt);
@@ -256,6 +260,8 @@ static int sort_common(void* keys, void* vals, int value_bytes, int64_t n, int d
   a.ws_bytes = ws_bytes;
   a.stream = static_cast<cudaStream_t>(stream);
   a.num_sms = num_sms();
+  a.host_keys = host_keys;
+  a.host_vals = value_bytes ? host_vals : nullptr;
   pdq_tuning tuned;
   if (!tuning && autotune_lookup(false, dt, value_bytes, n, 0, &tuned)) tuning = &tuned;
   int rc = make_tuning(tuning, &a.tune);
@@ -320,12 +326,18 @@ int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dt
   if (e == cudaSuccess && value_bytes)
     e = cudaMemcpyAsync(d_vals, h_vals, (size_t)n * value_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("H2D: ") + cudaGetErrorString(e));
-  int rc = sort_common(d_keys, d_vals, value_bytes, n, key_dtype, d_ws, ws_bytes, cuda_stream, tuning, stats);
+  // the sort itself copies every range of the result into the host arrays once it is final
+  // (n <= 1: nothing to sort, the arrays come back as they went)
+  int rc = n <= 1 ? PDQ_OK
+                  : sort_common(d_keys, d_vals, value_bytes, n, key_dtype, d_ws, ws_bytes, cuda_stream, tuning,
+                                stats, h_keys, h_vals);
   if (rc) return rc;
-  e = cudaMemcpyAsync(h_keys, d_keys, (size_t)n * kb, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && value_bytes)
-    e = cudaMemcpyAsync(h_vals, d_vals, (size_t)n * value_bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (n <= 1) {
+    e = cudaMemcpyAsync(h_keys, d_keys, (size_t)n * kb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && value_bytes)
+      e = cudaMemcpyAsync(h_vals, d_vals, (size_t)n * value_bytes, cudaMemcpyDeviceToHost, s);
+  }
+  e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_error(PDQ_ERR_CUDA, std::string("D2H: ") + cudaGetErrorString(e));
   return PDQ_OK;
 }

@@ -158,6 +158,8 @@ struct AuxStreams {
   cudaStream_t s[kBaseClasses];
   cudaEvent_t fork;
   cudaEvent_t join[kBaseClasses];
+  cudaStream_t copy;        // device-to-host copies of final ranges (host-buffer form)
+  cudaEvent_t ready, copied;
 };
 AuxStreams* aux_streams();
 bool profiling_enabled();  // per-kernel event timing is on: launches stay serial on their stream

@@ -31,6 +31,10 @@ struct SortArgs {
   cudaStream_t stream;
   Tuning tune;
   int num_sms;
+  // host-buffer form (pdq_sort_host): the sorted keys / values are copied here, each range as
+  // soon as it is final, while later ranges are still sorting (null: device result only)
+  void* host_keys = nullptr;
+  void* host_vals = nullptr;
 };
 
 // Byte offsets of the workspace regions.

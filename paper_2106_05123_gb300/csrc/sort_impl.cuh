@@ -176,10 +176,68 @@ class PlainSorter {
     bool done = false;
     int bad0 = 0;
     int rc = prologue(&done, &bad0);
-    if (rc || done) return rc;
+    if (rc) return rc;
+    if (done) return a_.host_keys ? stream_out(off_ + a_.n, true) : PDQ_OK;
     std::vector<Task> cur(1);
     cur[0] = Task{off_, a_.n, kBufKeys, 0, bad0, 0};
-    return level_loop(std::move(cur));
+    if (!a_.host_keys) return level_loop(std::move(cur));
+    return level_loop_streamed(std::move(cur));
+  }
+
+  // Host-buffer form: the first level over the whole array, then the next level's tasks in
+  // kStreamGroups position-ordered groups, each group sorted to the end.  Every element before
+  // the next group's first task is then final (it lies in a finished group or in a bucket the
+  // first level finished), so that range is copied to the host on a copy stream while the later
+  // groups sort.
+  static constexpr int kStreamGroups = 8;
+  int level_loop_streamed(std::vector<Task> cur) {
+    std::vector<Task> nxt;
+    ++stats_.passes;
+    int rc = level_round(cur.data(), 1, &nxt);
+    if (rc) return rc;
+    std::sort(nxt.begin(), nxt.end(), [](const Task& x, const Task& y) { return x.begin < y.begin; });
+    const size_t per = (nxt.size() + kStreamGroups - 1) / kStreamGroups;
+    int64_t deepest = 0;
+    for (size_t g0 = 0; g0 < nxt.size(); g0 += per) {
+      const size_t g1 = std::min(nxt.size(), g0 + per);
+      const int64_t before = stats_.passes;
+      rc = level_loop(std::vector<Task>(nxt.begin() + g0, nxt.begin() + g1));
+      if (rc) return rc;
+      deepest = std::max(deepest, stats_.passes - before);
+      stats_.passes = before;
+      rc = stream_out(g1 < nxt.size() ? nxt[g1].begin : off_ + a_.n, false);
+      if (rc) return rc;
+    }
+    stats_.passes += deepest;
+    return stream_out(off_ + a_.n, true);
+  }
+
+  // Copies [frontier_, end) of the keys (and values) to the host arrays after everything queued
+  // on the call's stream; `last`: the call's stream then waits for every copy.
+  int64_t frontier_ = -1;
+  int stream_out(int64_t end, bool last) {
+    if (frontier_ < 0) frontier_ = off_;
+    AuxStreams* aux = aux_streams();
+    cudaStream_t cs = st_;
+    if (aux) {
+      cs = aux->copy;
+      PDQ_CUDA(cudaEventRecord(aux->ready, st_));
+      PDQ_CUDA(cudaStreamWaitEvent(cs, aux->ready, 0));
+    }
+    if (end > frontier_) {
+      const int64_t e0 = frontier_ - off_, len = end - frontier_;
+      PDQ_CUDA(cudaMemcpyAsync(static_cast<U*>(a_.host_keys) + e0, keys_ + frontier_, (size_t)len * KS,
+                               cudaMemcpyDeviceToHost, cs));
+      if (VB)
+        PDQ_CUDA(cudaMemcpyAsync(static_cast<V*>(a_.host_vals) + e0, vals_ + frontier_, (size_t)len * VB,
+                                 cudaMemcpyDeviceToHost, cs));
+      frontier_ = end;
+    }
+    if (last && aux) {
+      PDQ_CUDA(cudaEventRecord(aux->copied, cs));
+      PDQ_CUDA(cudaStreamWaitEvent(st_, aux->copied, 0));
+    }
+    return PDQ_OK;
   }
 
   // Learned path (float32 keys): a trained monotone CDF model cuts the array into 4096
@@ -310,6 +368,7 @@ class PlainSorter {
       PDQ_LAUNCHED("learned_gather");
       {  // sort the sample with the plain path (its workspace is the part before the sample)
         SortArgs sa = a_;
+        sa.host_keys = sa.host_vals = nullptr;
         sa.keys = xs;
         sa.vals = nullptr;
         sa.n = m;
@@ -565,6 +624,7 @@ class PlainSorter {
     stats_.fixup_peeled = e_len;
     if (e_len > 1) {  // the marked keys' own sort (no fix-up inside it)
       SortArgs sa = a_;
+      sa.host_keys = sa.host_vals = nullptr;
       sa.keys = E;
       sa.vals = VB ? static_cast<void*>(Ev) : nullptr;
       sa.n = e_len;

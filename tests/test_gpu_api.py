@@ -105,3 +105,23 @@ def test_launch_count_and_kernel_profile():
     # values) read and written once
     assert prof["base_sort"][2] == pytest.approx(2 * 4 * n, rel=1e-2)
     assert np.array_equal(to_host(d, np.int32), oracle_sorted(a))
+
+
+@pytest.mark.parametrize("with_vals", [False, True])
+def test_sort_host_streams_ranges_of_a_two_level_sort(with_vals):
+    """Large enough for a second distribution level: the host-buffer call copies each
+    position-ordered group's range out while later groups sort; the result equals the oracle."""
+    n = (1 << 22) + 5
+    k = workloads.uniform_bits(n, np.int32, workloads.config_seed(95))
+    hk = torch.from_numpy(k.copy()).pin_memory()
+    dk = torch.empty_like(hk, device="cuda")
+    hv = dv = None
+    if with_vals:
+        hv = torch.arange(n, dtype=torch.int32).pin_memory()
+        dv = torch.empty_like(hv, device="cuda")
+    ws = pdq.workspace_for(n, torch.int32, 4 if with_vals else 0)
+    st = pdq.pdq_sort_host(hk, dk, ws, h_vals=hv, d_vals=dv)
+    assert st["passes"] >= 2
+    assert np.array_equal(hk.numpy(), oracle_sorted(k))
+    if with_vals:
+        assert np.array_equal(k[hv.numpy().astype(np.int64)], hk.numpy())
