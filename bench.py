@@ -202,6 +202,26 @@ def ncu_traffic(kernel: str, workload: str) -> float | None:
     return None
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu's "Model name", else /proc/cpuinfo), for the record."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
     """The CPU oracle (single-threaded, as it stands) on a bounded sample of the workload."""
     import oracle
@@ -218,6 +238,7 @@ def cpu_baseline(name: str, budget_s: float = 12.0) -> dict:
         reps += 1
     n_sample = inputs[0][0].size
     return {"value": total_keys / t_total / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(),
             "sample": f"{len(inputs)} array(s) of {n_sample} keys from the same generator, "
                       f"{reps} repetition(s), {t_total:.1f} s of single-core CPU time"}
 
@@ -286,7 +307,7 @@ def run_reference(args, rank: int) -> None:
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "description": desc, "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(), "sample": sample},
             "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -408,7 +429,8 @@ def bench_e2_sweep(args) -> None:
             "roofline": {"bound": "hbm", "kernel": "whole sort per cell (path_frac)", "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s"},
             "cpu_baseline": {"value": cpu_keys / cpu_s / 1e9 if cpu_s else None, "unit": "Gkeys/s", "cores": 1,
-                             "kind": "oracle", "sample": "every pattern at 2^10, 2^13, 2^16 keys"},
+                             "kind": "oracle", "cpu_model": host_cpu_model(), "host_cores": os.cpu_count(),
+                             "sample": "every pattern at 2^10, 2^13, 2^16 keys"},
             "e2e": None, "clocks": clocks, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
 
