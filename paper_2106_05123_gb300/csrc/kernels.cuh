@@ -1206,8 +1206,10 @@ __device__ __forceinline__ void radix_block_sort(uint32_t (&r)[ITEMS], uint32_t 
 }
 
 // The whole sort of one item by one CTA (blockDim.x == THREADS); `smem` holds
-// base_sort_smem<KS, VB, THREADS, ITEMS>() bytes, 16-byte aligned.
-template <int KT, int VB, int THREADS, int ITEMS>
+// base_sort_smem<KS, VB, THREADS, ITEMS>() bytes, 16-byte aligned (base_sort_core_smem when
+// RADIX is false: callers whose buckets rarely have a narrow code range, or that need the
+// shared memory for other work, keep the merge path only and a smaller footprint).
+template <int KT, int VB, int THREADS, int ITEMS, bool RADIX = true>
 __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>::U* __restrict__ keys,
                                                 typename Val<VB>::T* __restrict__ vals,
                                                 typename Key<KT>::U* __restrict__ tmpk,
@@ -1232,10 +1234,25 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   const V* srcv = W ? (it.buf == kBufKeys ? vals : tmpv) + it.begin : nullptr;
   bool max_code = false;  // a real code equal to the sentinel value (all ones)
   U mn = ~U(0), mx = U(0);  // range of the real codes
-  // Staging: slots [0, P + ITEMS) (ITEMS slack slots: harmless read-ahead of the merge) are
-  // covered by ITEMS + 1 strided slots per thread, as CAP + THREADS >= P + ITEMS.  All of a
-  // thread's global loads are issued before any is used, so their latency is paid once.
-  {
+  // Staging of slots [0, P + ITEMS) (ITEMS slack slots: harmless read-ahead of the merge).
+  // Merge-only callers stage with a plain strided loop (fewer live registers, more resident
+  // CTAs); with the radix path every thread covers ITEMS + 1 strided slots (CAP + THREADS >=
+  // P + ITEMS) and issues all of its global loads before using any, so their latency is paid once.
+  if constexpr (!RADIX) {
+    for (int i = tid; i < P + ITEMS; i += THREADS) {
+      U c = ~U(0);
+      if (i < m) {
+        const U x = srck[i];
+        c = it.enc ? x : Key<KT>::enc(x);
+        max_code |= c == ~U(0);
+        mn = c < mn ? c : mn;
+        mx = c > mx ? c : mx;
+        if (W) sv[i] = srcv[i];
+      }
+      sk[pad_idx<U>(i)] = c;
+      if (W) si[pad_idx<U>(i)] = (uint32_t)i;
+    }
+  } else {
     U xk[ITEMS + 1];
     V xv[W ? ITEMS + 1 : 1];
 #pragma unroll
@@ -1296,7 +1313,7 @@ __device__ __forceinline__ void base_sort_block(const Item& it, typename Key<KT>
   }
   const U span = mx - mn;
   const int nbits = (int)(8 * sizeof(U)) - (sizeof(U) == 4 ? __clz((uint32_t)span) : __clzll((uint64_t)span));
-  if constexpr (radix_fits<sizeof(U), VB, THREADS, ITEMS>()) {
+  if constexpr (RADIX && radix_fits<sizeof(U), VB, THREADS, ITEMS>()) {
    if (nbits <= kRadixMaxBits) {
     // narrow range: LSD counting passes on r = code - mn (padding r = 0xFFFFFF sorts last)
     uint32_t* arr = reinterpret_cast<uint32_t*>(sk);

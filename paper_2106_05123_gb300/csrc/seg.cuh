@@ -469,7 +469,9 @@ seg_persistent_kernel(typename Key<KT>::U* __restrict__ keys, typename Val<VB>::
       }
     } else if (t.kind == kSegBase) {
       const Item it{t.begin, t.size, (uint16_t)t.buf, (uint16_t)t.enc};
-      base_sort_block<KT, VB, THREADS, ITEMS>(it, keys, vals, tmpk, tmpv, kBufKeys, 1, smem);
+      // (rare: the bucket's size-class list was full) the merge path only, so that the base
+      // sort needs no more shared memory than the partition
+      base_sort_block<KT, VB, THREADS, ITEMS, false>(it, keys, vals, tmpk, tmpv, kBufKeys, 1, smem);
       if (tid == 0) atomicAdd(&st->base_buckets, 1ull);
     } else {
       seg_partition<KT, VB, THREADS>(t, prm, CAP, keys, vals, tmpk, tmpv, smem, wtmp, st, L);
@@ -496,14 +498,16 @@ seg_base_list_kernel(const Item* __restrict__ list, const unsigned long long* __
   const int64_t m = c < cap ? c : cap;
   for (int64_t k = blockIdx.x; k < m; k += gridDim.x) {
     const Item it = list[k];
-    base_sort_block<KT, VB, THREADS, ITEMS>(it, keys, vals, tmpk, tmpv, kBufKeys, 1, smem);
+    // segments hold raw keys whose codes span nearly the whole key width, so the radix path
+    // would rarely apply; without it the kernel keeps a smaller footprint and more CTAs per SM
+    base_sort_block<KT, VB, THREADS, ITEMS, false>(it, keys, vals, tmpk, tmpv, kBufKeys, 1, smem);
     __syncthreads();
   }
 }
 
 template <int KS, int VB, int THREADS, int ITEMS>
 constexpr size_t seg_smem() {
-  constexpr size_t base = base_sort_smem<KS, VB, THREADS, ITEMS>();
+  constexpr size_t base = base_sort_core_smem<KS, VB, THREADS, ITEMS>();
   constexpr size_t part = (size_t)(3 * kSegTile + 2 * kBMax) * KS + (size_t)3 * kSegTile * VB +
                          3 * kBinsMax * sizeof(uint32_t) + (size_t)kSegTile * 2;
   return base > part ? base : part;

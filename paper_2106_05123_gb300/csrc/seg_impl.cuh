@@ -176,11 +176,14 @@ class SegSorter {
   template <int CLS>
   int configure_class(int* grid) {
     constexpr int T = S::base_threads(CLS);
-    constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
+    constexpr size_t smem = base_sort_core_smem<KS, VB, T, S::kBaseItems>();
     static bool configured = false;
     if (!configured) {
       PDQ_CUDA(cudaFuncSetAttribute(seg_base_list_kernel<KT, VB, T, S::kBaseItems>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PDQ_CUDA(cudaFuncSetAttribute(seg_base_list_kernel<KT, VB, T, S::kBaseItems>,
+                                    cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    (int)cudaSharedmemCarveoutMaxShared));
       configured = true;
     }
     int per_sm = 0;
@@ -193,7 +196,7 @@ class SegSorter {
   int launch_class(int grid, const SegLists& lists, SegState* st, U* keys, V* vals, U* tmpk, V* tmpv,
                    cudaStream_t s) {
     constexpr int T = S::base_threads(CLS);
-    constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
+    constexpr size_t smem = base_sort_core_smem<KS, VB, T, S::kBaseItems>();
     seg_base_list_kernel<KT, VB, T, S::kBaseItems><<<grid, T, smem, s>>>(
         lists.blist[CLS], &st->n_blist[CLS], lists.bcap[CLS], keys, vals, tmpk, tmpv);
     PDQ_LAUNCHED("seg_base_list");
