@@ -10,14 +10,14 @@
 //   count_kernel      - branchless classification of every key into 2B bins: bin 2b holds keys
 //                       strictly between splitters b-1 and b, bin 2b+1 keys equal to splitter b
 //                       (the equal-key rule of Sec. 3)
-//   scan_totals_kernel - bucket starts per task; per-bin cursors the scatter reserves runs from
+//   scan_bookkeep_kernel - per task: bucket starts, per-bin cursors the scatter reserves runs
+//                       from, then the bookkeeping of the task's children: equal bins are
+//                       final; small bins go to the base sort; a bin keeping more than 7/8 of
+//                       its parent's non-equal keys is a bad split and decrements the subtree's
+//                       counter; at 0 the bin goes to the fallback (Sec. 4.1)
 //   scatter_kernel    - re-classifies a tile, ranks keys per bin with shared atomics, stages the
 //                       tile in shared memory grouped by bin and writes contiguous runs
 //                       (the GPU form of block partitioning, Sec. 5.3)
-//   bookkeep_kernel   - equal bins are final; small bins go to the base sort; a bin keeping
-//                       more than 7/8 of its parent's non-equal keys is a bad split and
-//                       decrements the subtree's counter; at 0 the bin goes to the fallback
-//                       (Sec. 4.1)
 //   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1): all-equal buckets are
 //                       copied, narrow code ranges take stable LSD counting passes, wide ones a
 //                       register-blocked merge sort
@@ -716,31 +716,6 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   }
 }
 
-// ================================================================== scan
-// One CTA per task: the exclusive scan of the task's bin totals gives every bin's first element
-// (relative to the task's first element); children[task * bin_stride + bin] = (start, size), and
-// the totals become the bins' write cursors, from which every scatter CTA reserves the run of
-// its chunk with one atomic per bin.  (Runs of different chunks land in a bin in the order of
-// their reservations: the sort is unstable, so any order is correct.)
-template <int THREADS, int MAXBINS>
-__global__ void __launch_bounds__(THREADS)
-scan_totals_kernel(const int32_t* __restrict__ task_nbins, uint32_t* __restrict__ totals, int bin_stride,
-                   uint2* __restrict__ children) {
-  __shared__ uint32_t tot[MAXBINS];
-  __shared__ uint32_t start[MAXBINS];
-  __shared__ uint32_t wtmp[THREADS / 32 + 1];
-  const int task = blockIdx.x;
-  const int nb = task_nbins[task];
-  uint32_t* t = totals + (size_t)task * bin_stride;
-  for (int b = threadIdx.x; b < nb; b += THREADS) tot[b] = t[b];
-  __syncthreads();
-  block_exclusive_scan<THREADS>(tot, start, nb, wtmp);
-  for (int b = threadIdx.x; b < nb; b += THREADS) {
-    children[(size_t)task * bin_stride + b] = make_uint2(start[b], tot[b]);
-    t[b] = start[b];
-  }
-}
-
 // ================================================================== scatter
 // One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE elements,
 // double-buffered in shared memory by bulk copy (the last window's sub-16-byte tail is fetched
@@ -958,30 +933,21 @@ __device__ __forceinline__ void warp_add(unsigned long long v, unsigned long lon
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
 }
 
-static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_nbins,
-                                const uint2* __restrict__ children, int bin_stride, int equal_bins,
-                                int base_cap, Counters* ctr,
-                                Task* __restrict__ next, Item* __restrict__ base_items,
-                                Item* __restrict__ copy_items, Item* __restrict__ fb_items,
-                                ListCaps caps) {
-  const int task = blockIdx.y;
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb = task_nbins[task];
-  const uint2 ch = b < nb ? children[(size_t)task * bin_stride + b] : make_uint2(0u, 0u);
-  const Task t = tasks[task];
-  // the parent's keys outside its equality bins (every block of the task sums them itself)
-  __shared__ unsigned long long s_equal;
-  if (threadIdx.x == 0) s_equal = 0ull;
-  __syncthreads();
-  if (equal_bins) {
-    unsigned long long e = 0ull;
-    for (int j = 2 * (int)threadIdx.x + 1; j < nb; j += 2 * (int)blockDim.x)
-      e += children[(size_t)task * bin_stride + j].y;
-    e = warp_sum(e);
-    if ((threadIdx.x & 31) == 0 && e) atomicAdd(&s_equal, e);
-  }
-  __syncthreads();
-  const int64_t nonequal = t.size - (int64_t)s_equal;
+// What becomes of child bin b = (start, size) of task t; every lane of the calling warp takes
+// part (list slots and counters are aggregated per warp).  nonequal: the parent's keys outside
+// its equality bins.
+struct BookLists {
+  Counters* ctr;
+  Task* next;
+  Item* base_items;
+  Item* copy_items;
+  Item* fb_items;
+  ListCaps caps;
+};
+
+__device__ __forceinline__ void bookkeep_child(const Task& t, int b, uint2 ch, int64_t nonequal, int equal_bins,
+                                               int base_cap, const BookLists& L) {
+  Counters* ctr = L.ctr;
   const int dst = t.buf == kBufKeys ? kBufTmp : kBufKeys;
   Item it;
   it.begin = t.begin + ch.x;
@@ -1013,11 +979,11 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
       else atomicAdd(&ctr->overflow, 1ull);
     }
   };
-  put(copy, copy_items, &ctr->n_copy, caps.copy_cap);
+  put(copy, L.copy_items, &ctr->n_copy, L.caps.copy_cap);
 #pragma unroll
   for (int c = 0; c < kBaseClasses; ++c)
-    put(base && cls == c, base_items + caps.base_off[c], &ctr->n_base[c], caps.base_cap[c]);
-  put(fallback, fb_items, &ctr->n_fallback, caps.fb_cap);
+    put(base && cls == c, L.base_items + L.caps.base_off[c], &ctr->n_base[c], L.caps.base_cap[c]);
+  put(fallback, L.fb_items, &ctr->n_fallback, L.caps.fb_cap);
   const unsigned long long k = warp_reserve(recurse, &ctr->n_next);
   if (recurse) {
     Task nt;
@@ -1027,8 +993,48 @@ static __global__ void bookkeep_kernel(const Task* __restrict__ tasks, const int
     nt.enc = 1;
     nt.bad_left = left;
     nt.attempt = t.attempt + 1;
-    if ((int64_t)k < caps.task_cap) next[k] = nt;
+    if ((int64_t)k < L.caps.task_cap) L.next[k] = nt;
     else atomicAdd(&ctr->overflow, 1ull);
+  }
+}
+
+// One CTA per task: the exclusive scan of the task's bin totals gives every bin's first element
+// (relative to the task's first element); the totals become the bins' write cursors, from which
+// every scatter CTA reserves the run of its chunk with one atomic per bin (runs of different
+// chunks land in a bin in the order of their reservations: the sort is unstable, so any order is
+// correct); children[task * bin_stride + bin] = (start, size).  The same CTA then does the
+// task's bookkeeping (bookkeep_child for every bin), so a level needs one launch for both.
+template <int THREADS, int MAXBINS>
+__global__ void __launch_bounds__(THREADS)
+scan_bookkeep_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_nbins,
+                     uint32_t* __restrict__ totals, int bin_stride, uint2* __restrict__ children, int equal_bins,
+                     int base_cap, BookLists L) {
+  __shared__ uint32_t tot[MAXBINS];
+  __shared__ uint32_t start[MAXBINS];
+  __shared__ uint32_t wtmp[THREADS / 32 + 1];
+  __shared__ unsigned long long s_equal;
+  const int task = blockIdx.x;
+  const int nb = task_nbins[task];
+  uint32_t* tt = totals + (size_t)task * bin_stride;
+  for (int b = threadIdx.x; b < nb; b += THREADS) tot[b] = tt[b];
+  if (threadIdx.x == 0) s_equal = 0ull;
+  __syncthreads();
+  block_exclusive_scan<THREADS>(tot, start, nb, wtmp);
+  unsigned long long e = 0ull;
+  for (int b = threadIdx.x; b < nb; b += THREADS) {
+    children[(size_t)task * bin_stride + b] = make_uint2(start[b], tot[b]);
+    tt[b] = start[b];
+    if (equal_bins && (b & 1)) e += tot[b];
+  }
+  e = warp_sum(e);
+  if ((threadIdx.x & 31) == 0 && e) atomicAdd(&s_equal, e);
+  __syncthreads();
+  const Task t = tasks[task];
+  const int64_t nonequal = t.size - (int64_t)s_equal;
+  for (int b0 = 0; b0 < nb; b0 += THREADS) {  // whole warps: the lists are reserved per warp
+    const int b = b0 + (int)threadIdx.x;
+    const uint2 ch = b < nb ? make_uint2(start[b], tot[b]) : make_uint2(0u, 0u);
+    bookkeep_child(t, b, ch, nonequal, equal_bins, base_cap, L);
   }
 }
 

@@ -413,7 +413,8 @@ class PlainSorter {
       PDQ_LAUNCHED("learned_count");
       {
         LaunchScope ls("learned_scan", st_, 0.0);
-        scan_totals_kernel<1024, kLearnedBuckets><<<1, 1024, 0, st_>>>(d_nb, totals_, kLearnedBuckets, children_);
+        scan_bookkeep_kernel<1024, kLearnedBuckets><<<1, 1024, 0, st_>>>(tasks_, d_nb, totals_, kLearnedBuckets,
+                                                                         children_, 0, cap_, book_lists());
       }
       PDQ_LAUNCHED("learned_scan");
       {
@@ -422,21 +423,6 @@ class PlainSorter {
             chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, totals_, ctr_);
       }
       PDQ_LAUNCHED("learned_scatter");
-      {
-        LaunchScope ls("bookkeep", st_, 0.0);
-        ListCaps caps;
-        for (int c = 0; c < kBaseClasses; ++c) {
-          caps.base_off[c] = L_.base_off[c];
-          caps.base_cap[c] = L_.base_cap[c];
-        }
-        caps.task_cap = L_.task_cap;
-        caps.copy_cap = L_.item_cap;
-        caps.fb_cap = L_.fb_cap;
-        dim3 grid((unsigned)(kLearnedBuckets + 255) / 256, 1);
-        bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_nb, children_, kLearnedBuckets, 0, cap_, ctr_, next_,
-                                                 base_items_, copy_items_, fb_items_, caps);
-      }
-      PDQ_LAUNCHED("bookkeep");
       Counters h;
       const int rc = finish_round(nxt, &h);
       stats_.learned_overflow = (int64_t)(h.n_next + h.n_fallback);
@@ -660,6 +646,24 @@ class PlainSorter {
     return PDQ_OK;
   }
 
+  // The bookkeeping's work lists and their capacities.
+  BookLists book_lists() const {
+    BookLists b;
+    b.ctr = ctr_;
+    b.next = next_;
+    b.base_items = base_items_;
+    b.copy_items = copy_items_;
+    b.fb_items = fb_items_;
+    for (int c = 0; c < kBaseClasses; ++c) {
+      b.caps.base_off[c] = L_.base_off[c];
+      b.caps.base_cap[c] = L_.base_cap[c];
+    }
+    b.caps.task_cap = L_.task_cap;
+    b.caps.copy_cap = L_.item_cap;
+    b.caps.fb_cap = L_.fb_cap;
+    return b;
+  }
+
   // Buckets per level: enough that the expected bucket is a quarter of the base capacity (so
   // that, with sampling noise, almost every bucket fits the base sort after this level).
   typename SplitterCls<U>::Params cls_params(const int32_t* d_logb) const {
@@ -680,9 +684,14 @@ class PlainSorter {
     return lb;
   }
 
-  // One distribution level over tasks[0..nt): sample, count, scan, scatter, bookkeeping, then
-  // base sorts / copies / fallbacks of the children that finished.  Next tasks are appended.
-  int level_round(const Task* tasks, int nt, std::vector<Task>* nxt) {
+  // The host-built part of a distribution round and its sample kernel: chunks, uploads of the
+  // task and chunk lists, counter resets, splitter selection.
+  struct Head {
+    int nchunks = 0;
+    int64_t total = 0;
+  };
+
+  int round_head(const Task* tasks, int nt, Head* hd) {
     const int64_t n = a_.n;
     int64_t total = 0;
     for (int i = 0; i < nt; ++i) total += tasks[i].size;
@@ -696,10 +705,8 @@ class PlainSorter {
     std::vector<int32_t> meta(4 * (size_t)nt);
     std::vector<Chunk> chunks;
     chunks.reserve((size_t)(total / ch + nt + 1));
-    int max_logb = 1;
     for (int i = 0; i < nt; ++i) {
       const int lb = choose_logb(tasks[i].size);
-      max_logb = std::max(max_logb, lb);
       meta[i] = lb;
       meta[nt + i] = (int32_t)chunks.size();
       const int64_t size = tasks[i].size;
@@ -713,9 +720,7 @@ class PlainSorter {
     }
     const int nchunks = (int)chunks.size();
     if (nchunks > L_.chunk_cap) return set_error(PDQ_ERR_INTERNAL, "chunk capacity exceeded");
-    int32_t* d_logb = meta_;
-    int32_t* d_c0 = meta_ + nt;
-    int32_t* d_nc = meta_ + 2 * nt;
+    int32_t* d_logb = meta_;        // meta: logb, first chunk, chunk count, bin count per task
     int32_t* d_nb = meta_ + 3 * nt;
     PDQ_CUDA(cudaMemcpyAsync(tasks_, tasks, sizeof(Task) * nt, cudaMemcpyHostToDevice, st_));
     PDQ_CUDA(cudaMemcpyAsync(meta_, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice, st_));
@@ -730,6 +735,22 @@ class PlainSorter {
           tasks_, d_logb, oversample, keys_, tmpk_, tree_, spl_, pref_, tab_);
     }
     PDQ_LAUNCHED("sample");
+    (void)d_nb;
+    hd->nchunks = nchunks;
+    hd->total = total;
+    return PDQ_OK;
+  }
+
+  // One distribution level over tasks[0..nt): sample, count, scan and bookkeeping, scatter, then
+  // base sorts / copies / fallbacks of the children that finished.  Next tasks are appended.
+  int level_round(const Task* tasks, int nt, std::vector<Task>* nxt) {
+    Head hd;
+    const int rc0 = round_head(tasks, nt, &hd);
+    if (rc0) return rc0;
+    const int nchunks = hd.nchunks;
+    const int64_t total = hd.total;
+    int32_t* d_logb = meta_;
+    int32_t* d_nb = meta_ + 3 * nt;
     {
       LaunchScope ls("count", st_, (double)total * KS);
       count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>
@@ -738,10 +759,11 @@ class PlainSorter {
     }
     PDQ_LAUNCHED("count");
     {
-      LaunchScope ls("scan", st_, 0.0);
-      scan_totals_kernel<512, kBinsMax><<<nt, 512, 0, st_>>>(d_nb, totals_, kBinsMax, children_);
+      LaunchScope ls("scan_bookkeep", st_, 0.0);
+      scan_bookkeep_kernel<512, kBinsMax><<<nt, 512, 0, st_>>>(tasks_, d_nb, totals_, kBinsMax, children_, 1,
+                                                               cap_, book_lists());
     }
-    PDQ_LAUNCHED("scan");
+    PDQ_LAUNCHED("scan_bookkeep");
     {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
       scatter_kernel<KT, VB, SplitterCls<U>, S::kScatterThreads, S::kScatterTile>
@@ -749,21 +771,6 @@ class PlainSorter {
               chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, totals_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
-    {
-      LaunchScope ls("bookkeep", st_, 0.0);
-      dim3 grid((unsigned)((2 << max_logb) + 255) / 256, (unsigned)nt);
-      ListCaps caps;
-      for (int c = 0; c < kBaseClasses; ++c) {
-        caps.base_off[c] = L_.base_off[c];
-        caps.base_cap[c] = L_.base_cap[c];
-      }
-      caps.task_cap = L_.task_cap;
-      caps.copy_cap = L_.item_cap;
-      caps.fb_cap = L_.fb_cap;
-      bookkeep_kernel<<<grid, 256, 0, st_>>>(tasks_, d_nb, children_, kBinsMax, 1, cap_, ctr_, next_,
-                                               base_items_, copy_items_, fb_items_, caps);
-    }
-    PDQ_LAUNCHED("bookkeep");
     Counters h;
     return finish_round(nxt, &h);
   }
