@@ -681,6 +681,12 @@ class PlainSorter {
     const int64_t want = (size + quarter - 1) / quarter;
     int lb = 1;
     while ((int64_t(1) << lb) < want && lb < a_.tune.logb) ++lb;
+    // Headroom on the last level: when the tuned width leaves buckets that fit the base sort on
+    // average but average above a third of its capacity (a parent well above the mean size),
+    // sampling noise can push one of them past the capacity and cost a whole further level; one
+    // more bit of buckets keeps the pass count of the sort the same from run to run.
+    if (lb == a_.tune.logb && lb < kLogBMax && size > ((int64_t)cap_ / 3 << lb) && size <= ((int64_t)cap_ << lb))
+      ++lb;
     return lb;
   }
 
