@@ -48,10 +48,14 @@ struct Chunk {
   int32_t task;       // index of the task in the round
 };
 
+// Base-sort lists can be split by position into this many groups (host-buffer sorts of large
+// arrays: each group's range goes back to the host as soon as its base sorts are done).
+constexpr int kOutGroups = 8;
+
 // Device-side counters written by the bookkeeping kernel.
 struct Counters {
   unsigned long long n_next;        // tasks for the next level
-  unsigned long long n_base[kBaseClasses];  // base-sort items per size class
+  unsigned long long n_base[kOutGroups][kBaseClasses];  // base-sort items per position group and size class
   unsigned long long n_copy;        // items to copy temp -> keys
   unsigned long long n_fallback;    // items for the merge-path fallback
   unsigned long long equal_buckets;
@@ -68,6 +72,11 @@ struct ListCaps {
   int64_t base_off[kBaseClasses];
   int64_t base_cap[kBaseClasses];
   int64_t task_cap, copy_cap, fb_cap;
+  // position groups of the base lists: an item starting at element b belongs to group
+  // floor((b - group_first) * groups / group_n); group g's lists start group_stride items after
+  // group g - 1's
+  int groups;
+  int64_t group_stride, group_first, group_n;
 };
 
 // ------------------------------------------------------------------ key encoding (ordered unsigned)

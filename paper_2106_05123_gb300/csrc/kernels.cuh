@@ -980,9 +980,17 @@ __device__ __forceinline__ void bookkeep_child(const Task& t, int b, uint2 ch, i
     }
   };
   put(copy, L.copy_items, &ctr->n_copy, L.caps.copy_cap);
+  int grp = 0;
+  if (L.caps.groups > 1) {
+    grp = (int)(((it.begin - L.caps.group_first) * L.caps.groups) / L.caps.group_n);
+    grp = grp < 0 ? 0 : (grp >= L.caps.groups ? L.caps.groups - 1 : grp);
+  }
+  for (int g = 0; g < L.caps.groups; ++g) {
+    Item* lists = L.base_items + (size_t)g * L.caps.group_stride;
 #pragma unroll
-  for (int c = 0; c < kBaseClasses; ++c)
-    put(base && cls == c, L.base_items + L.caps.base_off[c], &ctr->n_base[c], L.caps.base_cap[c]);
+    for (int c = 0; c < kBaseClasses; ++c)
+      put(base && cls == c && grp == g, lists + L.caps.base_off[c], &ctr->n_base[g][c], L.caps.base_cap[c]);
+  }
   put(fallback, L.fb_items, &ctr->n_fallback, L.caps.fb_cap);
   const unsigned long long k = warp_reserve(recurse, &ctr->n_next);
   if (recurse) {

@@ -44,6 +44,8 @@ struct Layout {
   int64_t task_cap, round_cap, chunk_cap, item_cap, fb_cap;
   int64_t base_off[5];  // first entry of each base-sort size class's list (in items)
   int64_t base_cap[5];  // capacity of each class's list
+  int64_t base_total;   // items of one position group's lists
+  int64_t base_groups;  // position groups of the base lists (1, or kOutGroups for large arrays)
   size_t learned_xs, learned_out, learned_sync;  // learned path only
   int64_t learned_m;
   // nearly-sorted fix-up (absent in nested sorts and below kFixMin elements): peeled keys and

@@ -67,7 +67,12 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
   L.children = take((size_t)L.round_cap * kBinsMax * sizeof(uint2));
   L.pref = take((size_t)L.round_cap * 32);
   L.tab = take((size_t)L.round_cap * kPrefTableBytes);
-  L.base_items = take((size_t)base_total * sizeof(Item));
+  // large arrays keep one set of base lists per position group (host-buffer sorts stream each
+  // group's range back as soon as it is sorted); 2^26 keys and up, where the lists are small
+  // beside the temp buffer
+  L.base_total = base_total;
+  L.base_groups = n >= (int64_t(1) << 26) ? kOutGroups : 1;
+  L.base_items = take((size_t)base_total * L.base_groups * sizeof(Item));
   L.copy_items = take((size_t)L.item_cap * sizeof(Item));
   L.fb_items = take((size_t)L.fb_cap * sizeof(Item));
   L.msplit = take((size_t)(n / 2048 + 2) * sizeof(int64_t));  // merge-path splits, one per 2048-output tile
@@ -170,6 +175,7 @@ class PlainSorter {
     copy_items_ = reinterpret_cast<Item*>(ws + L_.copy_items);
     fb_items_ = reinterpret_cast<Item*>(ws + L_.fb_items);
     st_ = a.stream;
+    groups_ = a.host_keys && L_.base_groups > 1 ? (int)L_.base_groups : 1;
   }
 
   int run() {
@@ -180,36 +186,9 @@ class PlainSorter {
     if (done) return a_.host_keys ? stream_out(off_ + a_.n, true) : PDQ_OK;
     std::vector<Task> cur(1);
     cur[0] = Task{off_, a_.n, kBufKeys, 0, bad0, 0};
-    if (!a_.host_keys) return level_loop(std::move(cur));
-    return level_loop_streamed(std::move(cur));
-  }
-
-  // Host-buffer form: the first level over the whole array, then the next level's tasks in
-  // kStreamGroups position-ordered groups, each group sorted to the end.  Every element before
-  // the next group's first task is then final (it lies in a finished group or in a bucket the
-  // first level finished), so that range is copied to the host on a copy stream while the later
-  // groups sort.
-  static constexpr int kStreamGroups = 8;
-  int level_loop_streamed(std::vector<Task> cur) {
-    std::vector<Task> nxt;
-    ++stats_.passes;
-    int rc = level_round(cur.data(), 1, &nxt);
-    if (rc) return rc;
-    std::sort(nxt.begin(), nxt.end(), [](const Task& x, const Task& y) { return x.begin < y.begin; });
-    const size_t per = (nxt.size() + kStreamGroups - 1) / kStreamGroups;
-    int64_t deepest = 0;
-    for (size_t g0 = 0; g0 < nxt.size(); g0 += per) {
-      const size_t g1 = std::min(nxt.size(), g0 + per);
-      const int64_t before = stats_.passes;
-      rc = level_loop(std::vector<Task>(nxt.begin() + g0, nxt.begin() + g1));
-      if (rc) return rc;
-      deepest = std::max(deepest, stats_.passes - before);
-      stats_.passes = before;
-      rc = stream_out(g1 < nxt.size() ? nxt[g1].begin : off_ + a_.n, false);
-      if (rc) return rc;
-    }
-    stats_.passes += deepest;
-    return stream_out(off_ + a_.n, true);
+    rc = level_loop(std::move(cur));
+    if (rc || !a_.host_keys) return rc;
+    return stream_out(off_ + a_.n, true);  // whatever the rounds did not send yet
   }
 
   // Copies [frontier_, end) of the keys (and values) to the host arrays after everything queued
@@ -271,6 +250,7 @@ class PlainSorter {
   SortArgs a_;
   Layout L_;
   int cap_;  // base capacity for this key/value width
+  int groups_ = 1;  // position groups of the base lists (host-buffer sorts of large arrays)
   int64_t off_ = 0;  // element shift of the key buffer from its 16-byte boundary
   bool vals_misaligned_ = false;
   U *keys_, *tmpk_, *tree_, *spl_;
@@ -334,7 +314,7 @@ class PlainSorter {
       ++stats_.passes;
       for (size_t r0 = 0; r0 < cur.size(); r0 += (size_t)L_.round_cap) {
         const size_t r1 = std::min(cur.size(), r0 + (size_t)L_.round_cap);
-        const int rc = level_round(cur.data() + r0, (int)(r1 - r0), &nxt);
+        const int rc = level_round(cur.data() + r0, (int)(r1 - r0), &nxt, r1 == cur.size());
         if (rc) return rc;
       }
       cur.swap(nxt);
@@ -661,6 +641,10 @@ class PlainSorter {
     b.caps.task_cap = L_.task_cap;
     b.caps.copy_cap = L_.item_cap;
     b.caps.fb_cap = L_.fb_cap;
+    b.caps.groups = groups_;
+    b.caps.group_stride = L_.base_total;
+    b.caps.group_first = off_;
+    b.caps.group_n = a_.n;
     return b;
   }
 
@@ -749,7 +733,7 @@ class PlainSorter {
 
   // One distribution level over tasks[0..nt): sample, count, scan and bookkeeping, scatter, then
   // base sorts / copies / fallbacks of the children that finished.  Next tasks are appended.
-  int level_round(const Task* tasks, int nt, std::vector<Task>* nxt) {
+  int level_round(const Task* tasks, int nt, std::vector<Task>* nxt, bool last_round = false) {
     Head hd;
     const int rc0 = round_head(tasks, nt, &hd);
     if (rc0) return rc0;
@@ -778,12 +762,12 @@ class PlainSorter {
     }
     PDQ_LAUNCHED("scatter");
     Counters h;
-    return finish_round(nxt, &h);
+    return finish_round(nxt, &h, last_round);
   }
 
   // After a round's bookkeeping: read the counters, sort finished buckets, copy final buckets
   // home, run fallbacks, and collect the next level's tasks.
-  int finish_round(std::vector<Task>* nxt, Counters* hout) {
+  int finish_round(std::vector<Task>* nxt, Counters* hout, bool last_round = false) {
     Counters& h = *hout;
     PDQ_CUDA(cudaMemcpyAsync(&h, ctr_, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
     PDQ_CUDA(cudaStreamSynchronize(st_));
@@ -792,34 +776,27 @@ class PlainSorter {
     stats_.equal_buckets += (int64_t)h.equal_buckets;
     stats_.bad_splits += (int64_t)h.bad_splits;
     // The size classes run concurrently on auxiliary streams forked from the call's stream and
-    // joined back before anything later on it (the next level's bookkeeping rewrites the lists).
-    // The level's base elements are counted once, on the first class launched.
+    // joined back before anything later on it (the next level's bookkeeping rewrites the lists);
+    // the copy of final buckets home runs meanwhile on the call's stream.  With position groups
+    // (host-buffer sorts of large arrays) the groups follow one another on each class's stream,
+    // and when this round finishes the sort, every group's range is copied to the host once its
+    // base sorts are done, while the later groups sort.  The level's base elements are counted
+    // once, on the first launch.
     int64_t base_elems = (int64_t)h.base_elems;
-    int nclasses = 0;
-    for (int cls = 0; cls < kBaseClasses; ++cls) nclasses += h.n_base[cls] ? 1 : 0;
+    int nlaunch = 0;
+    for (int g = 0; g < groups_; ++g)
+      for (int cls = 0; cls < kBaseClasses; ++cls) nlaunch += h.n_base[g][cls] ? 1 : 0;
+    const bool stream_now = a_.host_keys && groups_ > 1 && last_round && nxt->empty() && h.n_next == 0 &&
+                            h.n_fallback == 0;
     // (with per-kernel timing on they stay serial, so that each launch's time is its own)
-    AuxStreams* aux = nclasses > 1 && !profiling_enabled() ? aux_streams() : nullptr;
+    AuxStreams* aux = nlaunch > 1 && !profiling_enabled() ? aux_streams() : nullptr;
     if (aux && cudaEventRecord(aux->fork, st_) != cudaSuccess) aux = nullptr;
     bool joined[kBaseClasses] = {};
     auto join_all = [&]() {  // the call's stream waits for every class launched so far
       for (int cls = 0; cls < kBaseClasses; ++cls)
         if (joined[cls]) cudaStreamWaitEvent(st_, aux->join[cls], 0);
     };
-    for (int cls = 0; cls < kBaseClasses; ++cls) {
-      if (!h.n_base[cls]) continue;
-      cudaStream_t s = st_;
-      if (aux) {
-        s = aux->s[cls];
-        if (cudaStreamWaitEvent(s, aux->fork, 0) != cudaSuccess) s = st_;
-      }
-      const int rc = base_sort(cls, (int64_t)h.n_base[cls], kBufKeys, 1, base_elems, s);
-      if (s != st_ && cudaEventRecord(aux->join[cls], s) == cudaSuccess) joined[cls] = true;
-      if (rc) {
-        if (aux) join_all();
-        return rc;
-      }
-      base_elems = 0;
-    }
+    bool forked[kBaseClasses] = {};
     if (h.n_copy) {
       // The tile numbering lives in the counts region, free between a level's scatter and the
       // next level's count (item_cap + 1 words always fit: it holds at least 4096 bytes per task).
@@ -834,8 +811,33 @@ class PlainSorter {
       copy_kernel<KT, VB, 256, kCopyTile><<<(unsigned)blocks, 256, 0, st_>>>(
           copy_items_, (int)h.n_copy, tile0, keys_, vals_, tmpk_, tmpv_);
     }
-    if (aux) join_all();
     PDQ_LAUNCHED("copy");
+    for (int g = 0; g < groups_; ++g) {
+      for (int cls = 0; cls < kBaseClasses; ++cls) {
+        if (!h.n_base[g][cls]) continue;
+        cudaStream_t s = st_;
+        if (aux) {
+          s = aux->s[cls];
+          if (!forked[cls]) {
+            if (cudaStreamWaitEvent(s, aux->fork, 0) != cudaSuccess) s = st_;
+            else forked[cls] = true;
+          }
+        }
+        const int rc = base_sort(cls, (int64_t)h.n_base[g][cls], kBufKeys, 1, base_elems, s, g);
+        if (s != st_ && cudaEventRecord(aux->join[cls], s) == cudaSuccess) joined[cls] = true;
+        if (rc) {
+          if (aux) join_all();
+          return rc;
+        }
+        base_elems = 0;
+      }
+      if (stream_now) {  // everything before the next group's first element is final
+        if (aux) join_all();
+        const int rc = stream_out(off_ + (((int64_t)(g + 1) * a_.n + groups_ - 1) / groups_), false);
+        if (rc) return rc;
+      }
+    }
+    if (aux) join_all();
     if (h.n_fallback) {
       std::vector<Item> fb(h.n_fallback);
       PDQ_CUDA(cudaMemcpyAsync(fb.data(), fb_items_, sizeof(Item) * fb.size(), cudaMemcpyDeviceToHost, st_));
@@ -858,10 +860,10 @@ class PlainSorter {
   // Base sort of `count` items of size class `cls` (holding `elems` elements for the byte
   // accounting) already in that class's list.
   template <int CLS>
-  int base_sort_cls(int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st) {
+  int base_sort_cls(int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st, int group) {
     constexpr int T = S::base_threads(CLS);
     constexpr size_t smem = base_sort_smem<KS, VB, T, S::kBaseItems>();
-    const Item* list = base_items_ + L_.base_off[CLS];
+    const Item* list = base_items_ + (size_t)group * L_.base_total + L_.base_off[CLS];
     for (int64_t done = 0; done < count;) {
       const int64_t g = std::min<int64_t>(count - done, 1 << 30);
       LaunchScope ls("base_sort", st, done == 0 ? 2.0 * (double)elems * (KS + VB) : 0.0);
@@ -883,16 +885,17 @@ class PlainSorter {
     note_launch_count(1);
   }
 
-  int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st = nullptr) {
+  int base_sort(int cls, int64_t count, int out_buf, int decode, int64_t elems, cudaStream_t st = nullptr,
+                int group = 0) {
     stats_.base_buckets += count;
     if (!st) st = st_;
     switch (cls) {
-      case 0: return base_sort_cls<0>(count, out_buf, decode, elems, st);
-      case 1: return base_sort_cls<1>(count, out_buf, decode, elems, st);
-      case 2: return base_sort_cls<2>(count, out_buf, decode, elems, st);
-      case 3: return base_sort_cls<3>(count, out_buf, decode, elems, st);
+      case 0: return base_sort_cls<0>(count, out_buf, decode, elems, st, group);
+      case 1: return base_sort_cls<1>(count, out_buf, decode, elems, st, group);
+      case 2: return base_sort_cls<2>(count, out_buf, decode, elems, st, group);
+      case 3: return base_sort_cls<3>(count, out_buf, decode, elems, st, group);
       default:
-        if constexpr (S::kMaxClass >= 4) return base_sort_cls<4>(count, out_buf, decode, elems, st);
+        if constexpr (S::kMaxClass >= 4) return base_sort_cls<4>(count, out_buf, decode, elems, st, group);
         return set_error(PDQ_ERR_INTERNAL, "base class out of range");
     }
   }

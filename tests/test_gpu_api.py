@@ -109,9 +109,10 @@ def test_launch_count_and_kernel_profile():
 
 @pytest.mark.parametrize("with_vals", [False, True])
 def test_sort_host_streams_ranges_of_a_two_level_sort(with_vals):
-    """Large enough for a second distribution level: the host-buffer call copies each
-    position-ordered group's range out while later groups sort; the result equals the oracle."""
-    n = (1 << 22) + 5
+    """Large enough for a second distribution level and for position-grouped base lists (2^26
+    keys and up): the host-buffer call copies each group's range out as soon as its base sorts
+    are done, while later groups sort; the result equals the oracle."""
+    n = (1 << 26) + 5
     k = workloads.uniform_bits(n, np.int32, workloads.config_seed(95))
     hk = torch.from_numpy(k.copy()).pin_memory()
     dk = torch.empty_like(hk, device="cuda")
