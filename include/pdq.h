@@ -195,10 +195,13 @@ int pdq_learned_loss_grad(const float* d_x, const float* d_targets, int64_t m, c
 int pdq_learned_train(const float* d_xs, int64_t m, int steps, int batch, float lr, void* d_ws,
                       float* h_theta, float* h_norm_loss, float* h_wba, void* cuda_stream);
 
-/* Host-buffer convenience form of pdq_sort_keys / pdq_sort_pairs: copies h_keys (and h_vals
- * when value_bytes > 0) into the caller's device buffers d_keys / d_vals, sorts them there and
- * copies the result back into the host arrays, all on cuda_stream; returns after the stream
- * has finished.  Host arrays should be page-locked for full copy speed. */
+/* Host-buffer form of pdq_sort_keys / pdq_sort_pairs: copies h_keys (and h_vals when
+ * value_bytes > 0) into the caller's device buffers d_keys / d_vals, sorts them there and copies
+ * the result back into the host arrays, ordered on cuda_stream; returns after every copy has
+ * finished.  For 2^26 keys and more the result goes back range by range: the last round's base
+ * sorts run in position-ordered groups, and each group's range is copied to the host (on a
+ * library-owned copy stream, ordered by events) while the later groups sort.  Host arrays should
+ * be page-locked for full copy speed; they must not be touched until the call returns. */
 int pdq_sort_host(void* h_keys, void* h_vals, int value_bytes, int64_t n, pdq_dtype key_dtype,
                   void* d_keys, void* d_vals, void* d_ws, size_t ws_bytes, void* cuda_stream,
                   const pdq_tuning* tuning, pdq_stats* stats);
