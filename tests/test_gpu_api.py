@@ -126,3 +126,39 @@ def test_sort_host_streams_ranges_of_a_two_level_sort(with_vals):
     assert np.array_equal(hk.numpy(), oracle_sorted(k))
     if with_vals:
         assert np.array_equal(k[hv.numpy().astype(np.int64)], hk.numpy())
+
+
+@pytest.mark.parametrize("case", ["u64_pairs", "descending", "nearly_sorted"])
+def test_sort_host_large_other_paths(case):
+    """Host-buffer sorts of 2^26 + 3 elements through the other paths: 8-byte keys with 8-byte
+    values (position-grouped streaming), the reversal exit and the nearly-sorted fix-up (whose
+    result goes back in one piece at the end) — against the oracle."""
+    n = (1 << 26) + 3
+    if case == "u64_pairs":
+        k = workloads.uniform_bits(n, np.uint64, workloads.config_seed(96))
+        v = np.arange(n, dtype=np.uint64)
+        hk = torch.from_numpy(k.view(np.int64).copy()).pin_memory()
+        hv = torch.from_numpy(v.view(np.int64).copy()).pin_memory()
+        dk, dv = torch.empty_like(hk, device="cuda"), torch.empty_like(hv, device="cuda")
+        ws = pdq.workspace_for(n, torch.int64, 8)
+        st = pdq.lib().pdq_sort_host(hk.data_ptr(), hv.data_ptr(), 8, n, pdq.PDQ_U64, dk.data_ptr(),
+                                     dv.data_ptr(), ws.data_ptr(), ws.numel(), None, None, None)
+        assert st == 0, pdq.lib().pdq_last_error()
+        ok, ov = k.copy(), v.copy()
+        oracle.pdqsort_pairs(ok, ov)
+        got = hk.numpy().view(np.uint64)
+        assert np.array_equal(got, ok)
+        assert np.array_equal(k[hv.numpy().astype(np.int64)], got)
+        return
+    if case == "descending":
+        k = (n - 1 - np.arange(n)).astype(np.int32)
+    else:
+        k = workloads.pattern("asc_swaps", n, workloads.config_seed(97), dtype=np.int32)
+    hk = torch.from_numpy(k.copy()).pin_memory()
+    dk = torch.empty_like(hk, device="cuda")
+    st = pdq.pdq_sort_host(hk, dk, pdq.workspace_for(n, torch.int32))
+    assert np.array_equal(hk.numpy(), oracle_sorted(k))
+    if case == "descending":
+        assert st["reversed"] == 1
+    else:
+        assert st["fixup_peeled"] > 0
