@@ -9,15 +9,15 @@
 //                       samples per attempt (Sec. 4.2)
 //   count_kernel      - branchless classification of every key into 2B bins: bin 2b holds keys
 //                       strictly between splitters b-1 and b, bin 2b+1 keys equal to splitter b
-//                       (the equal-key rule of Sec. 3)
+//                       (the equal-key rule of Sec. 3); stores every key's bin slot
 //   scan_bookkeep_kernel - per task: bucket starts, per-bin cursors the scatter reserves runs
 //                       from, then the bookkeeping of the task's children: equal bins are
 //                       final; small bins go to the base sort; a bin keeping more than 7/8 of
 //                       its parent's non-equal keys is a bad split and decrements the subtree's
 //                       counter; at 0 the bin goes to the fallback (Sec. 4.1)
-//   scatter_kernel    - re-classifies a tile, ranks keys per bin with shared atomics, stages the
-//                       tile in shared memory grouped by bin and writes contiguous runs
-//                       (the GPU form of block partitioning, Sec. 5.3)
+//   scatter_kernel    - streams a tile with its stored bin slots, ranks keys per bin with shared
+//                       atomics, stages the tile in shared memory grouped by bin and writes
+//                       contiguous runs (the GPU form of block partitioning, Sec. 5.3)
 //   base_sort_kernel  - shared-memory sort of a small bucket (Sec. 5.1): all-equal buckets are
 //                       copied, narrow code ranges take stable LSD counting passes, wide ones a
 //                       register-blocked merge sort
@@ -572,6 +572,8 @@ struct SplitterCls {
     }
     return 2 * B;
   }
+  // The task's number of bins, without the shared state.
+  __device__ static int nbins(const Params& p, int task) { return 2 << p.task_logb[task]; }
   // Calls f(classifier) with a classifier specialised for the task's depth.
   template <class F>
   __device__ static void with(const Shared& sh, const Params&, F&& f) {
@@ -601,13 +603,15 @@ struct BinSlot {
 // into STAGES shared buffers by bulk copy; elements of a window outside the chunk are masked
 // (only the first and last window have any), and the last window's sub-16-byte tail is
 // classified straight from global memory.  Every code is classified and counted in a shared
-// histogram, written to counts[chunk][bin] at the end and added to the task's bin totals.
+// histogram, written to counts[chunk][bin] at the end and added to the task's bin totals.  Every
+// key's histogram slot is also stored (2 bytes, at the key's element index in `slots`), so that
+// the scatter reads the classification instead of repeating it.
 template <int KT, class CLS, int THREADS, int TILE, int STAGES>
 __global__ void __launch_bounds__(THREADS)
 count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
              const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
              typename CLS::Params cp, uint32_t* __restrict__ counts, int bin_stride,
-             uint32_t* __restrict__ totals, Counters* ctr) {
+             uint32_t* __restrict__ totals, uint16_t* __restrict__ slots, Counters* ctr) {
   using U = typename Key<KT>::U;
   constexpr int KS = sizeof(U);
   constexpr int VEC = 16 / KS;                // codes per 16-byte vector
@@ -649,7 +653,11 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   uint32_t parity = 0;
   bool failed = false;
   CLS::with(cs, cp, [&](auto classify) {
-    auto count_one = [&](U x) { atomicAdd(&hist[classify(enc ? x : Key<KT>::enc(x))], 1u); };
+    auto count_one = [&](U x, int64_t pos) {
+      const int sl = classify(enc ? x : Key<KT>::enc(x));
+      atomicAdd(&hist[sl], 1u);
+      slots[pos] = (uint16_t)sl;
+    };
     for (int tile = 0; tile < ntiles; ++tile) {
       const int stg = tile % STAGES;
       const int64_t ws = a0 + (int64_t)tile * TILE;
@@ -670,8 +678,16 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
           }
           int sl[VEC];
           classify.vec(v, sl);
+          uint16_t s16[VEC];
 #pragma unroll
-          for (int i = 0; i < VEC; ++i) atomicAdd(&hist[sl[i]], 1u);
+          for (int i = 0; i < VEC; ++i) {
+            atomicAdd(&hist[sl[i]], 1u);
+            s16[i] = (uint16_t)sl[i];
+          }
+          // the window starts on a 16-byte boundary of the keys, so these VEC slots are aligned
+          const int64_t pos = ws + (int64_t)(threadIdx.x + q * THREADS) * VEC;
+          if constexpr (VEC == 4) *reinterpret_cast<uint2*>(slots + pos) = *reinterpret_cast<const uint2*>(s16);
+          else *reinterpret_cast<uint32_t*>(slots + pos) = *reinterpret_cast<const uint32_t*>(s16);
         }
       } else {
         const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(wa - ws);
@@ -684,12 +700,12 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 #pragma unroll
           for (int i = 0; i < VEC; ++i) {
             const int k = vi * VEC + i;
-            if (k >= k0 && k < k1) count_one(v[i]);
+            if (k >= k0 && k < k1) count_one(v[i], ws + k);
           }
         }
         // sub-16-byte tail of the chunk, straight from global memory
         const int64_t g = (wa > cb ? wa : cb) + threadIdx.x;
-        if (g < we) count_one(src[g]);
+        if (g < we) count_one(src[g], g);
       }
       __syncthreads();  // this stage's buffer is consumed
       if (threadIdx.x == 0 && tile + STAGES < ntiles) {
@@ -720,17 +736,18 @@ count_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 // One CTA per chunk.  The chunk is cut into 16-byte-aligned windows of TILE elements,
 // double-buffered in shared memory by bulk copy (the last window's sub-16-byte tail is fetched
 // with plain loads a tile ahead and stored before use); elements outside the chunk are masked.
-// Per window: classify every code, rank it inside its bin with a shared atomic, scan the bin
-// counts, stage the window in place grouped by bin (codes and values), then write each bin's
-// run to its next free slots in the destination buffer (coalesced within runs).  Keys of an
-// equality bin written to the key buffer are final and are decoded on the way out.
+// Every key's bin slot comes from the count pass (`slots`, streamed in beside the keys), so the
+// scatter does no classification.  Per window: rank every code inside its bin with a shared
+// atomic, scan the bin counts, stage the window in place grouped by bin (codes and values), then
+// write each bin's run to its next free slots in the destination buffer (coalesced within runs).
+// Keys of an equality bin written to the key buffer are final and are decoded on the way out.
 template <int KT, int VB, class CLS, int THREADS, int TILE>
 __global__ void __launch_bounds__(THREADS, 2)  // two resident CTAs per SM: at most 64 registers
 scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
                typename Key<KT>::U* __restrict__ keys, typename Val<VB>::T* __restrict__ vals,
                typename Key<KT>::U* __restrict__ tmpk, typename Val<VB>::T* __restrict__ tmpv,
                typename CLS::Params cp, const uint32_t* __restrict__ counts, int bin_stride,
-               uint32_t* __restrict__ cursors, Counters* ctr) {
+               uint32_t* __restrict__ cursors, const uint16_t* __restrict__ slots, Counters* ctr) {
   using U = typename Key<KT>::U;
   using V = typename Val<VB>::T;
   constexpr int KS = sizeof(U);
@@ -749,14 +766,17 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
   uint32_t* hist = reinterpret_cast<uint32_t*>(smem + 2 * (KBUF + VBUF));  // per-window counts, then starts
   uint32_t* cursor = hist + NBMAX;                                         // next write offset per bin
   uint32_t* gbase = cursor + NBMAX;                                        // cursor - window start
-  uint16_t* stage_b = reinterpret_cast<uint16_t*>(gbase + NBMAX);
+  // two slot tiles, each the window widened to 8-element boundaries; a window's staged bin tags
+  // overwrite its own slot tile once every thread holds its slots
+  constexpr int SBUF = TILE + 16;
+  uint16_t* sbuf0 = reinterpret_cast<uint16_t*>(gbase + NBMAX);
+  auto sbuf = [&](int stg) { return sbuf0 + (size_t)stg * SBUF; };
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ typename CLS::Shared cs;
   __shared__ uint32_t wtmp[THREADS / 32 + 1];
 
   const Chunk c = chunks[blockIdx.x];
   const Task t = tasks[c.task];
-  const int nb = CLS::setup(cs, cp, c.task);
+  const int nb = CLS::nbins(cp, c.task);
   const BinSlot<CLS::kEqualBins> slot{__ffs(nb) - 2};  // hist, cursor, gbase and stage_b hold slots
   for (int b = threadIdx.x; b < nb; b += THREADS) {  // reserve this chunk's run in every bin
     const uint32_t cnt = counts[(size_t)blockIdx.x * bin_stride + b];
@@ -794,10 +814,14 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
     const int64_t wk = we - we % VK, wv = we - we % VV;
     if (threadIdx.x == 0) {
       const uint32_t kb = (uint32_t)((wk - ws) * KS), vb = VB ? (uint32_t)((wv - ws) * VS) : 0u;
+      // slots [ws rounded down to 8, we rounded up to 8): 16-byte aligned, inside the slot array
+      const int64_t s0 = ws & ~(int64_t)7, s1 = (we + 7) & ~(int64_t)7;
+      const uint32_t sbytes = (uint32_t)((s1 - s0) * 2);
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&bars[stg], kb + vb);
+      mbar_arrive_expect_tx(&bars[stg], kb + vb + sbytes);
       if (kb) bulk_g2s(kbuf(stg), srck + ws, kb, &bars[stg]);
       if (VB && vb) bulk_g2s(vbuf(stg), srcv + ws, vb, &bars[stg]);
+      if (sbytes) bulk_g2s(sbuf(stg), slots + s0, sbytes, &bars[stg]);
     }
     const int tid = threadIdx.x;
     if (tid < VK && wk + tid < we) {
@@ -814,97 +838,90 @@ scatter_kernel(const Chunk* __restrict__ chunks, const Task* __restrict__ tasks,
 
   uint32_t parity = 0;
   bool failed = false;
-  CLS::with(cs, cp, [&](auto classify) {
-    for (int tile = 0; tile < ntiles; ++tile) {
-      const int stg = tile & 1;
-      const int64_t ws = a0 + (int64_t)tile * TILE;
-      const int64_t we = ws + TILE < ce ? ws + TILE : ce;
-      const int64_t wk = we - we % VK, wv = we - we % VV;
-      const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(we - ws);  // valid buffer range
-      const int cnt = k1 - k0;
-      const bool full = k0 == 0 && k1 == TILE;
-      U* bk = kbuf(stg);
-      V* bv = VB ? vbuf(stg) : nullptr;
-      {
-        const int tid = threadIdx.x;
-        if (tid < VK && wk + tid < we) bk[wk - ws + tid] = stg ? pend_k1 : pend_k0;
-        if (VB && tid >= 32 && tid < 32 + VV && wv + (tid - 32) < we) bv[wv - ws + (tid - 32)] = stg ? pend_v1 : pend_v0;
-      }
-      const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
-      parity ^= 1u << stg;
-      if (!__syncthreads_and(ok)) { failed = true; break; }
-
-      U code[ITEMS];
-      V val[ITEMS];
-      uint32_t packed[ITEMS];  // slot << 16 | rank inside the bin; 0xFFFFFFFF for masked elements
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int vi = threadIdx.x + q * THREADS;
-        U v[VK];
-        *reinterpret_cast<uint4*>(v) = reinterpret_cast<const uint4*>(bk)[vi];
-#pragma unroll
-        for (int i = 0; i < VK; ++i) {
-          v[i] = enc ? v[i] : Key<KT>::enc(v[i]);
-          code[q * VK + i] = v[i];
-          if (VB) val[q * VK + i] = bv[vi * VK + i];
-        }
-        if (full) {  // interior window: classify the vector at once, no masks
-          int sl[VK];
-          classify.vec(v, sl);
-#pragma unroll
-          for (int i = 0; i < VK; ++i) packed[q * VK + i] = ((uint32_t)sl[i] << 16) | atomicAdd(&hist[sl[i]], 1u);
-        } else {
-#pragma unroll
-          for (int i = 0; i < VK; ++i) {
-            const int k = vi * VK + i;
-            if (k >= k0 && k < k1) {
-              const int sl = classify(v[i]);
-              packed[q * VK + i] = ((uint32_t)sl << 16) | atomicAdd(&hist[sl], 1u);
-            } else {
-              packed[q * VK + i] = 0xFFFFFFFFu;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      block_exclusive_scan<THREADS>(hist, hist, nb, wtmp, slot);  // hist := window start of each bin
-      for (int b = threadIdx.x; b < nb; b += THREADS) {
-        const int sl = slot(b);
-        const uint32_t start = hist[sl];
-        const uint32_t next = (b + 1 < nb) ? hist[slot(b + 1)] : (uint32_t)cnt;
-        gbase[sl] = cursor[sl] - start;
-        cursor[sl] += next - start;
-      }
-      // stage in place: every thread has read its codes from the buffer (scan barriers above)
-#pragma unroll
-      for (int e = 0; e < ITEMS; ++e) {
-        if (packed[e] != 0xFFFFFFFFu) {
-          const uint32_t sl = packed[e] >> 16;
-          const uint32_t p = hist[sl] + (packed[e] & 0xFFFFu);
-          bk[p] = code[e];
-          if (VB) bv[p] = val[e];
-          stage_b[p] = (uint16_t)sl;
-        }
-      }
-      __syncthreads();
-      auto write_one = [&](int i) {
-        const int b = stage_b[i];
-        const uint32_t o = gbase[b] + (uint32_t)i;
-        const U k = bk[i];
-        dstk[o] = (dst_is_keys && slot.equal(b)) ? Key<KT>::dec(k) : k;  // equality bin: final
-        if (VB) dstv[o] = bv[i];
-      };
-      if (full) {
-#pragma unroll
-        for (int r = 0; r < ITEMS; ++r) write_one(r * THREADS + threadIdx.x);
-      } else {
-        for (int i = threadIdx.x; i < cnt; i += THREADS) write_one(i);
-      }
-      __syncthreads();  // buffer, stage_b and hist are free again
-      for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
-      if (tile + 2 < ntiles) issue(tile + 2);
+  for (int tile = 0; tile < ntiles; ++tile) {
+    const int stg = tile & 1;
+    const int64_t ws = a0 + (int64_t)tile * TILE;
+    const int64_t we = ws + TILE < ce ? ws + TILE : ce;
+    const int64_t wk = we - we % VK, wv = we - we % VV;
+    const int k0 = (int)((cb > ws ? cb : ws) - ws), k1 = (int)(we - ws);  // valid buffer range
+    const int cnt = k1 - k0;
+    const bool full = k0 == 0 && k1 == TILE;
+    U* bk = kbuf(stg);
+    V* bv = VB ? vbuf(stg) : nullptr;
+    {
+      const int tid = threadIdx.x;
+      if (tid < VK && wk + tid < we) bk[wk - ws + tid] = stg ? pend_k1 : pend_k0;
+      if (VB && tid >= 32 && tid < 32 + VV && wv + (tid - 32) < we) bv[wv - ws + (tid - 32)] = stg ? pend_v1 : pend_v0;
     }
-  });
+    const bool ok = mbar_wait_bounded(&bars[stg], (parity >> stg) & 1u);
+    parity ^= 1u << stg;
+    if (!__syncthreads_and(ok)) { failed = true; break; }
+
+    U code[ITEMS];
+    V val[ITEMS];
+    uint32_t packed[ITEMS];  // slot << 16 | rank inside the bin; 0xFFFFFFFF for masked elements
+    const uint16_t* sw = sbuf(stg) + (ws & 7);  // slot of window element 0
+    uint16_t* stage_b = sbuf(stg);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int vi = threadIdx.x + q * THREADS;
+      U v[VK];
+      *reinterpret_cast<uint4*>(v) = reinterpret_cast<const uint4*>(bk)[vi];
+#pragma unroll
+      for (int i = 0; i < VK; ++i) {
+        v[i] = enc ? v[i] : Key<KT>::enc(v[i]);
+        code[q * VK + i] = v[i];
+        if (VB) val[q * VK + i] = bv[vi * VK + i];
+      }
+      // the window starts on a multiple of VA >= VK elements: the VK slots are aligned
+      uint16_t s16[VK];
+      if constexpr (VK == 4) *reinterpret_cast<uint2*>(s16) = *reinterpret_cast<const uint2*>(sw + vi * VK);
+      else *reinterpret_cast<uint32_t*>(s16) = *reinterpret_cast<const uint32_t*>(sw + vi * VK);
+#pragma unroll
+      for (int i = 0; i < VK; ++i) {
+        const int k = vi * VK + i;
+        const uint32_t sl = s16[i];
+        packed[q * VK + i] = (full || (k >= k0 && k < k1)) ? ((sl << 16) | atomicAdd(&hist[sl], 1u)) : 0xFFFFFFFFu;
+      }
+    }
+    __syncthreads();
+    block_exclusive_scan<THREADS>(hist, hist, nb, wtmp, slot);  // hist := window start of each bin
+    for (int b = threadIdx.x; b < nb; b += THREADS) {
+      const int sl = slot(b);
+      const uint32_t start = hist[sl];
+      const uint32_t next = (b + 1 < nb) ? hist[slot(b + 1)] : (uint32_t)cnt;
+      gbase[sl] = cursor[sl] - start;
+      cursor[sl] += next - start;
+    }
+    // stage in place: every thread has read its codes from the buffer (scan barriers above)
+#pragma unroll
+    for (int e = 0; e < ITEMS; ++e) {
+      if (packed[e] != 0xFFFFFFFFu) {
+        const uint32_t sl = packed[e] >> 16;
+        const uint32_t p = hist[sl] + (packed[e] & 0xFFFFu);
+        bk[p] = code[e];
+        if (VB) bv[p] = val[e];
+        stage_b[p] = (uint16_t)sl;
+      }
+    }
+    __syncthreads();
+    auto write_one = [&](int i) {
+      const int b = stage_b[i];
+      const uint32_t o = gbase[b] + (uint32_t)i;
+      const U k = bk[i];
+      dstk[o] = (dst_is_keys && slot.equal(b)) ? Key<KT>::dec(k) : k;  // equality bin: final
+      if (VB) dstv[o] = bv[i];
+    };
+    if (full) {
+#pragma unroll
+      for (int r = 0; r < ITEMS; ++r) write_one(r * THREADS + threadIdx.x);
+    } else {
+      for (int i = threadIdx.x; i < cnt; i += THREADS) write_one(i);
+    }
+    __syncthreads();  // buffer, stage_b and hist are free again
+    for (int b = threadIdx.x; b < nb; b += THREADS) hist[b] = 0;
+    if (tile + 2 < ntiles) issue(tile + 2);
+  }
   if (failed && threadIdx.x == 0) {
     atomicAdd(&ctr->timeout, 1ull);
     for (int i = 0; i < 2; ++i) mbar_wait_bounded(&bars[i], (parity >> i) & 1u);

@@ -57,6 +57,7 @@ struct ModelCls {
     int unused;
   };
   __device__ static int setup(Shared&, const Params& p, int) { return p.nbuckets; }
+  __device__ static int nbins(const Params& p, int) { return p.nbuckets; }
   struct Classifier {
     const LearnedModel& m;
     __device__ __forceinline__ int operator()(uint32_t code) const { return model_bucket(code, m); }

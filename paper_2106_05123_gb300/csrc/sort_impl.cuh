@@ -54,6 +54,9 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
   // temp buffers index like the (aligned-down) key buffer: up to 16 bytes of shift
   L.tmpk = take((size_t)(n + 16 / ks) * ks);
   L.tmpv = take((size_t)(n + (vb ? 16 / vb : 0)) * vb);
+  // every key's bin slot of the current level (2 bytes, indexed like the key buffer; the
+  // scatter's slot copies round out to 8-element boundaries past the last key)
+  L.slots = take((size_t)(n + 64) * sizeof(uint16_t));
   L.ctr = take(sizeof(Counters));
   L.tasks_cur = take((size_t)L.round_cap * sizeof(Task));
   L.tasks_next = take((size_t)L.task_cap * sizeof(Task));
@@ -99,12 +102,12 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
 template <int KS, int VB>
 struct Shape {
   // scatter: 512 threads, a 32 KiB tile of codes+values (power-of-two element count), double
-  // buffered, staged in place; plus 2 bytes of bin id per element
+  // buffered with its 2-byte bin slots (from the count pass), staged in place
   static constexpr int kScatterThreads = 512;
   static constexpr int kScatterTile = (KS + VB) <= 4 ? 8192 : ((KS + VB) <= 8 ? 4096 : 2048);
   static constexpr size_t kScatterSmem = 2 * ((size_t)kScatterTile * KS + (size_t)kScatterTile * VB) +
-                                         3 * (size_t)kBinsMax * 4 + (size_t)kScatterTile * 2;
-  // count: 512 threads, four 16 KiB tiles in flight
+                                         3 * (size_t)kBinsMax * 4 + 2 * ((size_t)kScatterTile + 16) * 2;
+  // count: 512 threads, three 16 KiB tiles in flight
   static constexpr int kCountThreads = 512;
   static constexpr int kCountTile = 16384 / KS;
   static constexpr int kCountStages = 3;
@@ -159,6 +162,7 @@ class PlainSorter {
     vals_misaligned_ = VB && ((uintptr_t)vals_ % 16) != 0;
     tmpk_ = reinterpret_cast<U*>(ws + L_.tmpk);
     tmpv_ = reinterpret_cast<V*>(ws + L_.tmpv);
+    slots_ = reinterpret_cast<uint16_t*>(ws + L_.slots);
     ctr_ = reinterpret_cast<Counters*>(ws + L_.ctr);
     tasks_ = reinterpret_cast<Task*>(ws + L_.tasks_cur);
     next_ = reinterpret_cast<Task*>(ws + L_.tasks_next);
@@ -259,6 +263,7 @@ class PlainSorter {
   Task *tasks_, *next_;
   int32_t* meta_;
   Chunk* chunks_;
+  uint16_t* slots_;
   uint32_t* counts_;
   uint32_t* totals_;  // per-(task, bin) key totals, turned into write cursors by the scan
   uint2* children_;
@@ -326,7 +331,8 @@ class PlainSorter {
   int learned_round(int bad0, std::vector<Task>* nxt) {
     if constexpr (KT == PDQ_F32 && VB == 0) {
       constexpr int kLTile = 4096;
-      constexpr size_t kLScatterSmem = 2 * (size_t)kLTile * 4 + 3 * (size_t)kLearnedBuckets * 4 + (size_t)kLTile * 2;
+      constexpr size_t kLScatterSmem =
+          2 * (size_t)kLTile * 4 + 3 * (size_t)kLearnedBuckets * 4 + 2 * ((size_t)kLTile + 16) * 2;
       static bool configured = false;
       if (!configured) {
         PDQ_CUDA(cudaFuncSetAttribute(count_kernel<KT, ModelCls, S::kCountThreads, S::kCountTile, S::kCountStages>,
@@ -388,7 +394,7 @@ class PlainSorter {
         LaunchScope ls("learned_count", st_, (double)n * KS);
         count_kernel<KT, ModelCls, S::kCountThreads, S::kCountTile, S::kCountStages>
             <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, model, counts_,
-                                                                kLearnedBuckets, totals_, ctr_);
+                                                                kLearnedBuckets, totals_, slots_, ctr_);
       }
       PDQ_LAUNCHED("learned_count");
       {
@@ -400,7 +406,8 @@ class PlainSorter {
       {
         LaunchScope ls("learned_scatter", st_, 2.0 * (double)n * KS);
         scatter_kernel<KT, 0, ModelCls, 512, kLTile><<<nchunks, 512, kLScatterSmem, st_>>>(
-            chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, totals_, ctr_);
+            chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, model, counts_, kLearnedBuckets, totals_, slots_,
+            ctr_);
       }
       PDQ_LAUNCHED("learned_scatter");
       Counters h;
@@ -745,7 +752,7 @@ class PlainSorter {
       LaunchScope ls("count", st_, (double)total * KS);
       count_kernel<KT, SplitterCls<U>, S::kCountThreads, S::kCountTile, S::kCountStages>
           <<<nchunks, S::kCountThreads, S::kCountSmem, st_>>>(chunks_, tasks_, keys_, tmpk_, cls_params(d_logb),
-                                                              counts_, kBinsMax, totals_, ctr_);
+                                                              counts_, kBinsMax, totals_, slots_, ctr_);
     }
     PDQ_LAUNCHED("count");
     {
@@ -758,7 +765,8 @@ class PlainSorter {
       LaunchScope ls("scatter", st_, 2.0 * (double)total * (KS + VB));
       scatter_kernel<KT, VB, SplitterCls<U>, S::kScatterThreads, S::kScatterTile>
           <<<nchunks, S::kScatterThreads, S::kScatterSmem, st_>>>(
-              chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, totals_, ctr_);
+              chunks_, tasks_, keys_, vals_, tmpk_, tmpv_, cls_params(d_logb), counts_, kBinsMax, totals_,
+              slots_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
     Counters h;
