@@ -1,6 +1,7 @@
 // C ABI of the library (see include/pdq.h): argument checks, dtype dispatch, error strings,
 // launch counting and the optional per-kernel event timing used for measurement.
 #include <nvtx3/nvToolsExt.h>
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -96,6 +97,29 @@ AuxStreams* aux_streams() {
     sets[dev] = a;
   }
   return sets[dev];
+}
+
+void* host_staging(int which, size_t bytes) {
+  struct Buf {  // kept until exit, like the auxiliary streams
+    void* p = nullptr;
+    size_t n = 0;
+  };
+  thread_local Buf bufs[2];
+  if (which < 0 || which > 1) return nullptr;
+  Buf& b = bufs[which];
+  if (b.n < bytes) {
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    const size_t want = std::max<size_t>(bytes, 64 * 1024);
+    if (cudaHostAlloc(&b.p, want, cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return nullptr;
+    }
+    b.n = want;
+  }
+  return b.p;
 }
 
 GraphCache& graph_cache() {

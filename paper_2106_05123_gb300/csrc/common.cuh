@@ -171,6 +171,11 @@ struct AuxStreams {
   cudaEvent_t ready, copied;
 };
 AuxStreams* aux_streams();
+// Pinned host staging of the calling thread (portable across devices), at least `bytes` long;
+// `which` selects one of two independent buffers (0: uploads, 1: counter read-backs).  A
+// caller must not reuse a buffer before the copies from or into it have completed.  Null if
+// pinned memory cannot be had (callers then use pageable memory).
+void* host_staging(int which, size_t bytes);
 bool profiling_enabled();  // per-kernel event timing is on: launches stay serial on their stream
 
 struct LaunchScope {

@@ -389,18 +389,26 @@ __device__ __forceinline__ int eytz_inorder(int j, int logb) {
 // One CTA per task.  Draws ns = min(oversample * B, kMaxSamples) keys at hashed positions
 // (SplitMix64 of a seed derived from the task's range and attempt), sorts them with a bitonic
 // network in shared memory and takes every (ns/B)-th as a splitter.  A value drawn many times
-// repeats as a splitter: its keys all go to its equality bin.
+// repeats as a splitter: its keys all go to its equality bin.  It also clears what the round's
+// later kernels accumulate into: the task's bin totals, and (CTA 0) the round's counters up to
+// the probe results.
 template <int KT, int THREADS>
 __global__ void __launch_bounds__(THREADS)
 sample_kernel(const Task* __restrict__ tasks, const int32_t* __restrict__ task_logb, int oversample,
               const typename Key<KT>::U* __restrict__ keys, const typename Key<KT>::U* __restrict__ tmp,
               typename Key<KT>::U* __restrict__ tree_out, typename Key<KT>::U* __restrict__ spl_out,
-              Pref<typename Key<KT>::U>* __restrict__ pref_out, PrefEnt* __restrict__ tab_out) {
+              Pref<typename Key<KT>::U>* __restrict__ pref_out, PrefEnt* __restrict__ tab_out,
+              Counters* __restrict__ ctr, uint32_t* __restrict__ totals, int bin_stride) {
   using U = typename Key<KT>::U;
   __shared__ U s[kMaxSamples];
   const Task t = tasks[blockIdx.x];
   const int logb = task_logb[blockIdx.x];
   const int B = 1 << logb;
+  for (int b = threadIdx.x; b < 2 * B; b += THREADS) totals[(size_t)blockIdx.x * bin_stride + b] = 0u;
+  if (blockIdx.x == 0) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(ctr);
+    for (int i = threadIdx.x; i < (int)(offsetof(Counters, probe) / 8); i += THREADS) w[i] = 0ull;
+  }
   int ns = oversample * B;
   if (ns > kMaxSamples) ns = kMaxSamples;
   if (ns < B) ns = B;

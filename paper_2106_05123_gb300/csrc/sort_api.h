@@ -39,8 +39,9 @@ struct SortArgs {
 
 // Byte offsets of the workspace regions.
 struct Layout {
-  size_t tmpk, tmpv, slots, ctr, tasks_cur, tasks_next, task_meta, chunks, counts, totals, tree, spl, children,
-      pref, tab, base_items, copy_items, fb_items, msplit, total;
+  // round_in: one round's task list, per-task metadata and chunk list, uploaded in one copy
+  size_t tmpk, tmpv, slots, ctr, round_in, tasks_next, counts, totals, tree, spl, children, pref, tab,
+      base_items, copy_items, fb_items, msplit, total;
   int64_t task_cap, round_cap, chunk_cap, item_cap, fb_cap;
   int64_t base_off[5];  // first entry of each base-sort size class's list (in items)
   int64_t base_cap[5];  // capacity of each class's list

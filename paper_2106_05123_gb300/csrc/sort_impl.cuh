@@ -28,6 +28,14 @@ constexpr int64_t kFixMin = int64_t(1) << 16;  // smallest array given the nearl
 constexpr int kFixTile = 8192;                 // elements per tile of the fix-up's peel pass
 constexpr int kCopyTile = 8192;                // elements per tile of the copy of final buckets home
 
+// A round's upload: nt tasks, then 4 int32 of metadata per task, then the chunks (16-byte
+// aligned parts).
+inline size_t round_in_meta_off(int64_t nt) { return align_up((size_t)nt * sizeof(Task), 16); }
+inline size_t round_in_chunks_off(int64_t nt) { return align_up(round_in_meta_off(nt) + (size_t)nt * 16, 16); }
+inline size_t round_in_bytes(int64_t nt, int64_t nchunks) {
+  return round_in_chunks_off(nt) + (size_t)nchunks * sizeof(Chunk);
+}
+
 inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool fixup = true) {
   Layout L;
   std::memset(&L, 0, sizeof(L));
@@ -58,10 +66,8 @@ inline Layout make_layout(int64_t n, int ks, int vb, bool learned = false, bool 
   // scatter's slot copies round out to 8-element boundaries past the last key)
   L.slots = take((size_t)(n + 64) * sizeof(uint16_t));
   L.ctr = take(sizeof(Counters));
-  L.tasks_cur = take((size_t)L.round_cap * sizeof(Task));
+  L.round_in = take(round_in_bytes(L.round_cap, L.chunk_cap));
   L.tasks_next = take((size_t)L.task_cap * sizeof(Task));
-  L.task_meta = take((size_t)L.round_cap * 4 * sizeof(int32_t));
-  L.chunks = take((size_t)L.chunk_cap * sizeof(Chunk));
   L.counts = take((size_t)L.chunk_cap * kBinsMax * sizeof(uint32_t));
   // per-(task, bin) totals, then write cursors (the learned level has one task of 4096 bins)
   L.totals = take((size_t)std::max<int64_t>(L.round_cap * kBinsMax, 4096) * sizeof(uint32_t));
@@ -164,10 +170,9 @@ class PlainSorter {
     tmpv_ = reinterpret_cast<V*>(ws + L_.tmpv);
     slots_ = reinterpret_cast<uint16_t*>(ws + L_.slots);
     ctr_ = reinterpret_cast<Counters*>(ws + L_.ctr);
-    tasks_ = reinterpret_cast<Task*>(ws + L_.tasks_cur);
+    round_in_ = ws + L_.round_in;
+    set_round_in(L_.round_cap);
     next_ = reinterpret_cast<Task*>(ws + L_.tasks_next);
-    meta_ = reinterpret_cast<int32_t*>(ws + L_.task_meta);
-    chunks_ = reinterpret_cast<Chunk*>(ws + L_.chunks);
     counts_ = reinterpret_cast<uint32_t*>(ws + L_.counts);
     totals_ = reinterpret_cast<uint32_t*>(ws + L_.totals);
     tree_ = reinterpret_cast<U*>(ws + L_.tree);
@@ -188,8 +193,14 @@ class PlainSorter {
     int rc = prologue(&done, &bad0);
     if (rc) return rc;
     if (done) return a_.host_keys ? stream_out(off_ + a_.n, true) : PDQ_OK;
-    std::vector<Task> cur(1);
-    cur[0] = Task{off_, a_.n, kBufKeys, 0, bad0, 0};
+    std::vector<Task> cur;
+    if (spec_ready_) {  // the first level already ran with the probe: finish it
+      ++stats_.passes;
+      rc = finish_round(&cur, &spec_h_, true, true);
+      if (rc) return rc;
+    } else {
+      cur.push_back(Task{off_, a_.n, kBufKeys, 0, bad0, 0});
+    }
     rc = level_loop(std::move(cur));
     if (rc || !a_.host_keys) return rc;
     return stream_out(off_ + a_.n, true);  // whatever the rounds did not send yet
@@ -229,6 +240,7 @@ class PlainSorter {
   int run_learned() {
     bool done = false;
     int bad0 = 0;
+    allow_spec_ = false;
     int rc = prologue(&done, &bad0);
     if (rc || done) return rc;
     std::vector<Task> nxt;
@@ -260,9 +272,16 @@ class PlainSorter {
   U *keys_, *tmpk_, *tree_, *spl_;
   V *vals_, *tmpv_;
   Counters* ctr_;
-  Task *tasks_, *next_;
+  Task *tasks_, *next_;  // tasks_, meta_ and chunks_ point into round_in_ (set_round_in)
   int32_t* meta_;
   Chunk* chunks_;
+  char* round_in_;
+  // Points tasks_, meta_ and chunks_ at their parts of the upload region for nt tasks.
+  void set_round_in(int64_t nt) {
+    tasks_ = reinterpret_cast<Task*>(round_in_);
+    meta_ = reinterpret_cast<int32_t*>(round_in_ + round_in_meta_off(nt));
+    chunks_ = reinterpret_cast<Chunk*>(round_in_ + round_in_chunks_off(nt));
+  }
   uint16_t* slots_;
   uint32_t* counts_;
   uint32_t* totals_;  // per-(task, bin) key totals, turned into write cursors by the scan
@@ -291,8 +310,17 @@ class PlainSorter {
                                cudaMemcpyHostToDevice, st_));
       return base_sort(cls, 1, kBufKeys, 1, n);
     }
+    const int bad0 = a_.tune.bad_allowed > 0 ? a_.tune.bad_allowed
+                                              : (a_.tune.bad_allowed < 0 ? 0 : ilog2_floor((uint64_t)n));
     if (a_.tune.probe) {
       bool sorted = false, nearly = false;
+      rc = speculate(bad0);
+      if (rc) return rc;
+      if (spec_ready_) {
+        *done = false;
+        *bad0_out = bad0;
+        return PDQ_OK;
+      }
       rc = probe(&sorted, &nearly);
       if (rc || sorted) return rc;
       if (nearly) {
@@ -301,8 +329,6 @@ class PlainSorter {
         if (rc || fixed) return rc;
       }
     }
-    const int bad0 = a_.tune.bad_allowed > 0 ? a_.tune.bad_allowed
-                                              : (a_.tune.bad_allowed < 0 ? 0 : ilog2_floor((uint64_t)n));
     if (bad0 == 0) {
       Item it{off_, (uint32_t)n, kBufKeys, 0};
       ++stats_.fallback_buckets;
@@ -384,6 +410,7 @@ class PlainSorter {
       const int nchunks = (int)chunks.size();
       const Task root{off_, n, kBufKeys, 0, bad0, 0};
       const int32_t meta[4] = {0, 0, nchunks, kLearnedBuckets};  // logb (unused), chunk0, nchunks, nbins
+      set_round_in(L_.round_cap);  // (the chunk part then has room for chunk_cap chunks)
       PDQ_CUDA(cudaMemcpyAsync(tasks_, &root, sizeof(Task), cudaMemcpyHostToDevice, st_));
       PDQ_CUDA(cudaMemcpyAsync(meta_, meta, sizeof(meta), cudaMemcpyHostToDevice, st_));
       PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
@@ -457,36 +484,75 @@ class PlainSorter {
 
   // Sorted / reverse probe (Sec. 5.2): a sample first, the full pass only when the sample is
   // monotone.  Sets *done when the array needs nothing more.
+  // Queues the probe over every stride-th key (results in ctr_->probe: descents, ascents, ...).
+  int launch_probe(int64_t stride) {
+    const int64_t n = a_.n;
+    const unsigned long long init[4] = {0, 0, ~0ull, 0};
+    PDQ_CUDA(cudaMemcpyAsync(ctr_->probe, init, sizeof(init), cudaMemcpyHostToDevice, st_));
+    const int64_t m = (n - 1) / stride + 1;
+    const int threads = 256;
+    int blocks = (int)std::min<int64_t>((m + threads - 1) / threads, (int64_t)a_.num_sms * 8);
+    if (blocks < 1) blocks = 1;
+    {
+      LaunchScope ls("probe", st_, (double)m * KS);
+      probe_kernel<KT><<<blocks, threads, 0, st_>>>(keys_ + off_, n, stride, m, ctr_->probe);
+    }
+    PDQ_LAUNCHED("probe");
+    return PDQ_OK;
+  }
+
+  static int64_t probe_stride(int64_t n) { return std::max<int64_t>(1, n / 65536); }
+
+  // Whether the sampled probe's descents h0 and ascents h1 (over m_sample strided pairs) send the
+  // array to the ordinary sort: the sample is neither monotone, and its descents are not few (at
+  // most 1/16 of its pairs) yet scattered (at least 1/256: not a handful of long ascending runs,
+  // whose boundaries the fix-up cannot repair) -- such an array is probed in full for the fix-up.
+  bool sample_says_sort(unsigned long long h0, unsigned long long h1, int64_t m_sample) const {
+    const bool can_fix = a_.tune.fixup && L_.fix_m > 0;
+    return h0 != 0 && h1 != 0 && !(can_fix && (int64_t)h0 * 16 <= m_sample && (int64_t)h0 * 256 >= m_sample);
+  }
+
+  // Small arrays (up to kSpecMax keys, with a sampled probe): the probe's sample and the whole
+  // first level are queued back to back, and one read-back of the counters (which hold the probe
+  // results too) serves both, instead of one synchronisation after each.  The first level only
+  // reads the keys and writes the temporary buffers, lists and counters, so when the probe asks
+  // for anything but the ordinary sort (sorted, reversed, the fix-up), its work is dropped and
+  // the usual path runs from the probe on.  Sets spec_ready_ (with spec_h_) when it was kept.
+  static constexpr int64_t kSpecMax = int64_t(1) << 22;
+  bool allow_spec_ = true;  // (the learned path replaces the first level: no speculation)
+  bool spec_ready_ = false;
+  Counters spec_h_{};
+  int speculate(int bad0) {
+    const int64_t n = a_.n;
+    const int64_t stride = probe_stride(n);
+    if (!allow_spec_ || n > kSpecMax || stride < 2 || bad0 <= 0) return PDQ_OK;
+    int rc = launch_probe(stride);
+    if (rc) return rc;
+    const Task root{off_, n, kBufKeys, 0, bad0, 0};
+    rc = launch_round(&root, 1);
+    if (rc) return rc;
+    rc = read_counters(&spec_h_);
+    if (rc) return rc;
+    if (sample_says_sort(spec_h_.probe[0], spec_h_.probe[1], (n - 1) / stride + 1)) spec_ready_ = true;
+    return PDQ_OK;
+  }
+
   int probe(bool* done, bool* nearly) {
     const int64_t n = a_.n;
     const bool can_fix = a_.tune.fixup && L_.fix_m > 0;
     unsigned long long h[4];
     auto run_probe = [&](int64_t stride) -> int {
-      const unsigned long long init[4] = {0, 0, ~0ull, 0};
-      PDQ_CUDA(cudaMemcpyAsync(ctr_->probe, init, sizeof(init), cudaMemcpyHostToDevice, st_));
-      const int64_t m = (n - 1) / stride + 1;
-      const int threads = 256;
-      int blocks = (int)std::min<int64_t>((m + threads - 1) / threads, (int64_t)a_.num_sms * 8);
-      if (blocks < 1) blocks = 1;
-      {
-        LaunchScope ls("probe", st_, (double)m * KS);
-        probe_kernel<KT><<<blocks, threads, 0, st_>>>(keys_ + off_, n, stride, m, ctr_->probe);
-      }
-      PDQ_LAUNCHED("probe");
+      const int rc = launch_probe(stride);
+      if (rc) return rc;
       PDQ_CUDA(cudaMemcpyAsync(h, ctr_->probe, sizeof(h), cudaMemcpyDeviceToHost, st_));
       PDQ_CUDA(cudaStreamSynchronize(st_));
       return PDQ_OK;
     };
-    const int64_t stride = std::max<int64_t>(1, n / 65536);
+    const int64_t stride = probe_stride(n);
     int rc = run_probe(stride);
     if (rc) return rc;
     const int64_t m_sample = (n - 1) / stride + 1;
-    // The sample is neither monotone: sort, unless its descents are few (at most 1/16 of its
-    // pairs) yet scattered (at least 1/256: not a handful of long ascending runs, whose
-    // boundaries the fix-up cannot repair) -- then probe the whole array for the fix-up.
-    if (stride > 1 && h[0] != 0 && h[1] != 0 &&
-        !(can_fix && (int64_t)h[0] * 16 <= m_sample && (int64_t)h[0] * 256 >= m_sample))
-      return PDQ_OK;
+    if (stride > 1 && sample_says_sort(h[0], h[1], m_sample)) return PDQ_OK;
     if (stride > 1) {
       rc = run_probe(1);
       if (rc) return rc;
@@ -717,19 +783,29 @@ class PlainSorter {
     }
     const int nchunks = (int)chunks.size();
     if (nchunks > L_.chunk_cap) return set_error(PDQ_ERR_INTERNAL, "chunk capacity exceeded");
-    int32_t* d_logb = meta_;        // meta: logb, first chunk, chunk count, bin count per task
+    // one upload of tasks, metadata (logb, first chunk, chunk count, bin count per task) and
+    // chunks, from pinned staging when there is some (every round ends with a synchronisation
+    // of the call's stream, so the staging is free again when the next round fills it)
+    set_round_in(nt);
+    const size_t bytes = round_in_bytes(nt, nchunks);
+    char* stage = static_cast<char*>(host_staging(0, bytes));
+    std::vector<char> pageable;
+    if (!stage) {
+      pageable.resize(bytes);
+      stage = pageable.data();
+    }
+    std::memcpy(stage, tasks, sizeof(Task) * nt);
+    std::memcpy(stage + round_in_meta_off(nt), meta.data(), sizeof(int32_t) * meta.size());
+    std::memcpy(stage + round_in_chunks_off(nt), chunks.data(), sizeof(Chunk) * nchunks);
+    PDQ_CUDA(cudaMemcpyAsync(round_in_, stage, bytes, cudaMemcpyHostToDevice, st_));
+    int32_t* d_logb = meta_;
     int32_t* d_nb = meta_ + 3 * nt;
-    PDQ_CUDA(cudaMemcpyAsync(tasks_, tasks, sizeof(Task) * nt, cudaMemcpyHostToDevice, st_));
-    PDQ_CUDA(cudaMemcpyAsync(meta_, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice, st_));
-    PDQ_CUDA(cudaMemcpyAsync(chunks_, chunks.data(), sizeof(Chunk) * nchunks, cudaMemcpyHostToDevice, st_));
-    PDQ_CUDA(cudaMemsetAsync(ctr_, 0, offsetof(Counters, probe), st_));
-    PDQ_CUDA(cudaMemsetAsync(totals_, 0, sizeof(uint32_t) * kBinsMax * (size_t)nt, st_));
 
     int oversample = a_.tune.oversample;
-    {
+    {  // (it also clears the round's counters and bin totals)
       LaunchScope ls("sample", st_, 0.0);
       sample_kernel<KT, S::kSampleThreads><<<nt, S::kSampleThreads, 0, st_>>>(
-          tasks_, d_logb, oversample, keys_, tmpk_, tree_, spl_, pref_, tab_);
+          tasks_, d_logb, oversample, keys_, tmpk_, tree_, spl_, pref_, tab_, ctr_, totals_, kBinsMax);
     }
     PDQ_LAUNCHED("sample");
     (void)d_nb;
@@ -741,6 +817,14 @@ class PlainSorter {
   // One distribution level over tasks[0..nt): sample, count, scan and bookkeeping, scatter, then
   // base sorts / copies / fallbacks of the children that finished.  Next tasks are appended.
   int level_round(const Task* tasks, int nt, std::vector<Task>* nxt, bool last_round = false) {
+    const int rc = launch_round(tasks, nt);
+    if (rc) return rc;
+    Counters h;
+    return finish_round(nxt, &h, last_round);
+  }
+
+  // Queues one distribution level over tasks[0..nt): sample, count, scan and bookkeeping, scatter.
+  int launch_round(const Task* tasks, int nt) {
     Head hd;
     const int rc0 = round_head(tasks, nt, &hd);
     if (rc0) return rc0;
@@ -769,16 +853,28 @@ class PlainSorter {
               slots_, ctr_);
     }
     PDQ_LAUNCHED("scatter");
-    Counters h;
-    return finish_round(nxt, &h, last_round);
+    return PDQ_OK;
+  }
+
+  // Reads the round's counters back (through pinned staging when there is some) and waits for
+  // the call's stream.
+  int read_counters(Counters* h) {
+    Counters* hc = static_cast<Counters*>(host_staging(1, sizeof(Counters)));
+    PDQ_CUDA(cudaMemcpyAsync(hc ? hc : h, ctr_, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
+    PDQ_CUDA(cudaStreamSynchronize(st_));
+    if (hc) *h = *hc;
+    return PDQ_OK;
   }
 
   // After a round's bookkeeping: read the counters, sort finished buckets, copy final buckets
   // home, run fallbacks, and collect the next level's tasks.
-  int finish_round(std::vector<Task>* nxt, Counters* hout, bool last_round = false) {
+  // have_counters: *hout already holds them.
+  int finish_round(std::vector<Task>* nxt, Counters* hout, bool last_round = false, bool have_counters = false) {
     Counters& h = *hout;
-    PDQ_CUDA(cudaMemcpyAsync(&h, ctr_, sizeof(Counters), cudaMemcpyDeviceToHost, st_));
-    PDQ_CUDA(cudaStreamSynchronize(st_));
+    if (!have_counters) {
+      const int rc = read_counters(&h);
+      if (rc) return rc;
+    }
     if (h.timeout) return set_error(PDQ_ERR_TIMEOUT, "a tile copy did not complete within its bounded wait");
     if (h.overflow) return set_error(PDQ_ERR_INTERNAL, "bookkeeping list capacity exceeded");
     stats_.equal_buckets += (int64_t)h.equal_buckets;
