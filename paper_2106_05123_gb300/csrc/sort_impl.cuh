@@ -758,11 +758,11 @@ class PlainSorter {
     const int64_t n = a_.n;
     int64_t total = 0;
     for (int i = 0; i < nt; ++i) total += tasks[i].size;
-    // Chunks: one task is cut into one chunk per resident count CTA (4 per SM, one wave; the
-    // scatter runs two per SM, two waves).  Several tasks cannot share chunks, so each task is
-    // cut into equal parts of at most about total / (2 waves) elements: two near-full waves
-    // instead of one full wave and a ragged tail.
-    const int64_t slots = (int64_t)a_.num_sms * 4;
+    // Chunks: one task is cut into 6 chunks per SM, whole waves of both the count (3 resident
+    // CTAs per SM with 4-byte keys, 2 with 8-byte keys) and the scatter (2 per SM).  Several
+    // tasks cannot share chunks, so each task is cut into equal parts of at most about total /
+    // (2 x 6 per SM) elements: near-full waves instead of full ones and a ragged tail.
+    const int64_t slots = (int64_t)a_.num_sms * 6;
     const int64_t want = nt == 1 ? slots : 2 * slots;
     const int64_t ch = std::max<int64_t>(chunk_min_for(n), (total + want - 1) / want);
     std::vector<int32_t> meta(4 * (size_t)nt);
