@@ -482,8 +482,6 @@ class PlainSorter {
     return PDQ_OK;
   }
 
-  // Sorted / reverse probe (Sec. 5.2): a sample first, the full pass only when the sample is
-  // monotone.  Sets *done when the array needs nothing more.
   // Queues the probe over every stride-th key (results in ctr_->probe: descents, ascents, ...).
   int launch_probe(int64_t stride) {
     const int64_t n = a_.n;
@@ -537,6 +535,8 @@ class PlainSorter {
     return PDQ_OK;
   }
 
+  // Sorted / reverse probe (Sec. 5.2): a sample first, the full pass only when the sample is
+  // monotone or has few scattered descents.  Sets *done when the array needs nothing more.
   int probe(bool* done, bool* nearly) {
     const int64_t n = a_.n;
     const bool can_fix = a_.tune.fixup && L_.fix_m > 0;
