@@ -29,7 +29,10 @@
  *     once without touching the device.
  *   - Workspace: caller-provided device memory of at least pdq_workspace_bytes(...) bytes,
  *     256-byte aligned.  The library allocates no device memory of its own, except the
- *     segmented path's CUDA-graph cache (see pdq_sort_segmented).
+ *     segmented path's CUDA-graph cache (see pdq_sort_segmented).  On host memory it keeps,
+ *     per calling thread and until exit, two small pinned staging buffers (64 KiB or the size
+ *     of one level's task and chunk lists) for its uploads and counter read-backs; without
+ *     pinned memory it falls back to pageable copies.
  *   - n must be < 2^32.  n = 0 and n = 1 are no-ops.  value_bytes is 4 or 8.
  *   - d_keys and d_vals need their natural alignment.  Internally tiles are staged by 16-byte
  *     bulk copies from the 16-byte boundary at or below d_keys (up to 12 bytes before d_keys are
