@@ -55,6 +55,16 @@ def test_workspace_bytes_is_host_logic(L):
         assert (pdq.pdq_workspace_bytes(1 << 20, code, 0, num_segments=300)
                 == pdq.pdq_workspace_bytes(1 << 20, pdq.PDQ_U64, 0, num_segments=300))
     assert pdq.pdq_workspace_bytes(10, pdq.PDQ_I32, 3) == 0
+    # the temp key buffer plus every key's 2-byte bin slot of the current level
+    assert big >= (4 + 2) * (1 << 20) and wide >= (8 + 2) * (1 << 20)
+
+
+def test_noalloc_limit_fits_its_fixed_array(L):
+    """pdq_sort_keys_noalloc promises every key type up to 2^20 keys inside its fixed 64 MiB
+    device array: the keys-only workspace at that size must fit for every type."""
+    import paper_2106_05123_gb300 as pdq
+    for code in (pdq.PDQ_I32, pdq.PDQ_U32, pdq.PDQ_F32, pdq.PDQ_I64, pdq.PDQ_U64, pdq.PDQ_I32I32, pdq.PDQ_F32U32):
+        assert 0 < pdq.pdq_workspace_bytes(1 << 20, code, 0) <= 64 << 20, code
 
 
 def test_argument_errors_need_no_device(L):
