@@ -108,10 +108,11 @@ void* host_staging(int which, size_t bytes) {
   if (which < 0 || which > 1) return nullptr;
   Buf& b = bufs[which];
   if (b.n < bytes) {
+    // grow geometrically: each reallocation frees pinned memory, which synchronises the device
+    const size_t want = std::max<size_t>(bytes, std::max<size_t>(64 * 1024, 2 * b.n));
     if (b.p) cudaFreeHost(b.p);
     b.p = nullptr;
     b.n = 0;
-    const size_t want = std::max<size_t>(bytes, 64 * 1024);
     if (cudaHostAlloc(&b.p, want, cudaHostAllocPortable) != cudaSuccess) {
       cudaGetLastError();
       b.p = nullptr;
